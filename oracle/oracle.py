@@ -1,0 +1,210 @@
+"""ctypes front end of the FP64 CPU oracle (resample_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg. It never touches the CUDA library and the CUDA
+library never touches it.
+
+Layouts: images are HWC (H, W, C) float64 arrays; planar NCHW tensors are
+viewed as one HWC image with N*C interleaved channels (marshalling only: the
+arithmetic is identical per channel).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "resample_oracle.c"
+BUILD = HERE / "_build"
+LIB = BUILD / "liboracle.so"
+
+NEAREST, BILINEAR, BICUBIC = 0, 1, 2
+ASYMMETRIC, HALF_PIXEL = 0, 1
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (OpenMP when available)."""
+    if LIB.exists() and not force and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB
+    BUILD.mkdir(exist_ok=True)
+    tmp = BUILD / f"liboracle.{os.getpid()}.so"
+    base = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
+            str(SRC), "-o", str(tmp), "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # The mutation tests point this at a deliberately broken build.
+        override = os.environ.get("RESAMPLE_ORACLE_LIB")
+        if override:
+            path = override
+        else:
+            build()
+            path = str(LIB)
+        L = ctypes.CDLL(path)
+        P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.oracle_resize_f64.argtypes = [P, I64, I64, I64, P, I64, I64, I, I, D]
+        L.oracle_resize_points_f64.argtypes = [P, I64, I64, I64, I64, I64, I, I, D,
+                                               P, P, I64, P]
+        L.oracle_bilinear_eq5_f64.argtypes = [P, I64, I64, P, I64, I64]
+        L.oracle_adjoint_f64.argtypes = [P, I64, I64, I64, P, I64, I64, I, I, D]
+        L.oracle_axis_matrix.argtypes = [I64, I64, I, I, D, P]
+        L.oracle_axis_taps.argtypes = [I64, I64, I, I, D, P, P]
+        L.oracle_quantize_u8.argtypes = [P, I64, P]
+        L.oracle_to_f16_bits.argtypes = [P, I64, P]
+        L.oracle_to_bf16_bits.argtypes = [P, I64, P]
+        L.oracle_tile_of_pixel.argtypes = [I64, I64, I64, I64, P, P, P, P]
+        L.oracle_num_threads.restype = I
+        L.oracle_set_num_threads.argtypes = [I]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _hwc(src: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(src, dtype=np.float64)
+    if a.ndim == 2:
+        a = a[:, :, None]
+    return a
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().oracle_set_num_threads(int(n))
+
+
+def resize(src, Ho: int, Wo: int, method: int, coord: int = ASYMMETRIC,
+           a: float = -0.5) -> np.ndarray:
+    """FP64 resampling of an (H, W) or (H, W, C) image; returns (Ho, Wo, C)."""
+    x = _hwc(src)
+    H, W, C = x.shape
+    out = np.empty((Ho, Wo, C), np.float64)
+    lib().oracle_resize_f64(_p(x), H, W, C, _p(out), Ho, Wo, method, coord, a)
+    return out
+
+
+def resize_points(src, Ho: int, Wo: int, method: int, coord: int, a: float,
+                  ys, xs) -> np.ndarray:
+    """FP64 outputs at the points (ys[k], xs[k]); returns (npts, C)."""
+    x = _hwc(src)
+    H, W, C = x.shape
+    ys = np.ascontiguousarray(ys, np.int64)
+    xs = np.ascontiguousarray(xs, np.int64)
+    out = np.empty((len(ys), C), np.float64)
+    lib().oracle_resize_points_f64(_p(x), H, W, C, Ho, Wo, method, coord, a,
+                                   _p(ys), _p(xs), len(ys), _p(out))
+    return out
+
+
+def resize_nchw(x, Ho: int, Wo: int, method: int, coord: int = ASYMMETRIC,
+                a: float = -0.5) -> np.ndarray:
+    N, C, H, W = x.shape
+    hwc = np.ascontiguousarray(np.asarray(x, np.float64).reshape(N * C, H, W).transpose(1, 2, 0))
+    y = resize(hwc, Ho, Wo, method, coord, a)
+    return np.ascontiguousarray(y.transpose(2, 0, 1).reshape(N, C, Ho, Wo))
+
+
+def bilinear_eq5(src2d, Ho: int, Wo: int) -> np.ndarray:
+    x = np.ascontiguousarray(src2d, np.float64)
+    H, W = x.shape
+    out = np.empty((Ho, Wo), np.float64)
+    lib().oracle_bilinear_eq5_f64(_p(x), H, W, _p(out), Ho, Wo)
+    return out
+
+
+def adjoint(gy, H: int, W: int, method: int, coord: int = ASYMMETRIC,
+            a: float = -0.5) -> np.ndarray:
+    """Transpose of resize(): (Ho, Wo, C) output gradient -> (H, W, C)."""
+    g = _hwc(gy)
+    Ho, Wo, C = g.shape
+    out = np.empty((H, W, C), np.float64)
+    lib().oracle_adjoint_f64(_p(g), Ho, Wo, C, _p(out), H, W, method, coord, a)
+    return out
+
+
+def adjoint_nchw(gy, H: int, W: int, method: int, coord: int = ASYMMETRIC,
+                 a: float = -0.5) -> np.ndarray:
+    N, C, Ho, Wo = gy.shape
+    hwc = np.ascontiguousarray(np.asarray(gy, np.float64).reshape(N * C, Ho, Wo).transpose(1, 2, 0))
+    g = adjoint(hwc, H, W, method, coord, a)
+    return np.ascontiguousarray(g.transpose(2, 0, 1).reshape(N, C, H, W))
+
+
+def axis_matrix(n: int, m: int, method: int, coord: int = ASYMMETRIC,
+                a: float = -0.5) -> np.ndarray:
+    A = np.empty((m, n), np.float64)
+    lib().oracle_axis_matrix(n, m, method, coord, a, _p(A))
+    return A
+
+
+def axis_taps(n: int, m: int, method: int, coord: int = ASYMMETRIC, a: float = -0.5):
+    idx = np.empty((m, 4), np.int64)
+    w = np.empty((m, 4), np.float64)
+    lib().oracle_axis_taps(n, m, method, coord, a, _p(idx), _p(w))
+    return idx, w
+
+
+def quantize_u8(v) -> np.ndarray:
+    x = np.ascontiguousarray(v, np.float64)
+    out = np.empty(x.shape, np.uint8)
+    lib().oracle_quantize_u8(_p(x), x.size, _p(out))
+    return out
+
+
+def to_f16_bits(v) -> np.ndarray:
+    x = np.ascontiguousarray(v, np.float64)
+    out = np.empty(x.shape, np.uint16)
+    lib().oracle_to_f16_bits(_p(x), x.size, _p(out))
+    return out
+
+
+def to_bf16_bits(v) -> np.ndarray:
+    x = np.ascontiguousarray(v, np.float64)
+    out = np.empty(x.shape, np.uint16)
+    lib().oracle_to_bf16_bits(_p(x), x.size, _p(out))
+    return out
+
+
+def bf16_bits_to_f64(bits) -> np.ndarray:
+    b = np.ascontiguousarray(bits, np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
+
+
+def store(v, dtype: str) -> np.ndarray:
+    """Round FP64 values to a storage dtype. Returns uint8, float16, uint16
+    (bfloat16 bit patterns) or float32 arrays."""
+    if dtype == "u8":
+        return quantize_u8(v)
+    if dtype == "f16":
+        return to_f16_bits(v).view(np.float16)
+    if dtype == "bf16":
+        return to_bf16_bits(v)
+    if dtype == "f32":
+        return np.asarray(v, np.float64).astype(np.float32)
+    raise ValueError(dtype)
+
+
+def tile_of_pixel(px: int, py: int, bw: int, bh: int):
+    vals = [ctypes.c_int64() for _ in range(4)]
+    lib().oracle_tile_of_pixel(px, py, bw, bh, *[ctypes.addressof(v) for v in vals])
+    return tuple(v.value for v in vals)  # (bx, by, tx, ty)
