@@ -1,0 +1,215 @@
+/*
+ * resample.h -- C ABI of the GB300 image-resampling library (libresample.so).
+ *
+ * The library resamples 2-D images by nearest-neighbour, bilinear or bicubic
+ * interpolation on one GPU. The operation is the paper's image resizing
+ * (Sec. II.B, Eqs. 1-5): every output pixel (x_f, y_f) maps to the source
+ * point x_p = x_f / scale, y_p = y_f / scale (Eq. 1), takes the neighbours
+ * int(x_p), int(x_p) + 1 (Eqs. 2-3) with fractional offsets (Eq. 4) and
+ * blends them (Eq. 5). The paper names nearest-neighbour and bicubic
+ * interpolation without defining them; the library defines them as follows.
+ *
+ *   Per axis, for output index j of m outputs from n source samples:
+ *   - scale is m / n, taken from the sizes, so x = j * n / m exactly
+ *     (RS_COORD_ASYMMETRIC, the paper's Eq. 1); RS_COORD_HALF_PIXEL maps
+ *     pixel centres instead: x = (j + 1/2) * n / m - 1/2;
+ *   - i0 = floor(x), t = x - i0 (Eqs. 2-4);
+ *   - RS_NEAREST: sample i0 (asymmetric) or floor(x + 1/2) (half-pixel);
+ *     RS_BILINEAR: samples i0, i0+1, weights 1-t, t (Eq. 5);
+ *     RS_BICUBIC: samples i0-1 .. i0+2, weights K(t+1), K(t), K(1-t), K(2-t)
+ *     with Keys' cubic convolution kernel K of parameter a (default -1/2);
+ *   - every sample index is clamped to [0, n-1] (edge replicate).
+ *   The 2-D result is the product of the two axes' weights summed over the
+ *   taps, per channel. Arithmetic is FP32 (weights and accumulation) for
+ *   every storage type. Stores round to nearest even; uint8 stores clamp to
+ *   [0, 255] first.
+ *
+ * Conventions shared by every entry point:
+ *   - All image pointers are DEVICE pointers the caller owns. The library
+ *     never allocates, frees or synchronises caller memory or streams.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream). RS_OK means the work was enqueued.
+ *   - Arguments are validated on the host before anything is launched. On
+ *     any error status nothing is launched and no output is written.
+ *   - Sizes: 1 <= H, W, Ho, Wo <= 65535. Strides are in ELEMENTS.
+ *   - Inputs and outputs must not overlap (RS_ERR_INVALID_ARG).
+ *   - Thread-safe for distinct streams. Calls on one stream run in order.
+ *   - RS_ERR_CUDA reports a launch or runtime error; rs_last_cuda_error()
+ *     returns its CUDA error code for the calling thread.
+ */
+#ifndef RESAMPLE_H
+#define RESAMPLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = 1,   /* null pointer, size out of range, overlap, bad stride */
+    RS_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
+    RS_ERR_ALIGNMENT = 3,     /* pointer not aligned to its element size */
+    RS_ERR_WORKSPACE = 4,     /* workspace null or smaller than required */
+    RS_ERR_CUDA = 5           /* CUDA launch / runtime error */
+} rs_status;
+
+typedef enum { RS_U8 = 0, RS_F16 = 1, RS_BF16 = 2, RS_F32 = 3 } rs_dtype;
+typedef enum { RS_NEAREST = 0, RS_BILINEAR = 1, RS_BICUBIC = 2 } rs_method;
+typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
+
+/* Kernel selection. AUTO = the tiled kernel with the tuned (or default)
+ * configuration. PLAIN = one thread per output pixel reading its taps from
+ * global memory, thread blocks of tile_w x tile_h threads (default 32 x 4):
+ * the paper's kernel (Sec. III.A, Eq. 6), kept as the comparison baseline. */
+typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2 } rs_impl;
+
+typedef struct {
+    int32_t coord;      /* rs_coord; default RS_COORD_ASYMMETRIC */
+    float cubic_a;      /* Keys parameter a for RS_BICUBIC; default -0.5 */
+    int32_t impl;       /* rs_impl; default RS_IMPL_AUTO */
+    int32_t tile_w;     /* 0 = default. PLAIN: threads per block along x.
+                           TILED: output elements per tile row (multiple of 4*32). */
+    int32_t tile_h;     /* 0 = default. PLAIN: threads along y. TILED: output rows per tile. */
+    int32_t threads;    /* 0 = default. TILED: threads per block (128 or 256). */
+    int32_t reserved[2];
+} rs_options;
+
+/* Fills *opt with the defaults listed above. */
+void rs_options_init(rs_options* opt);
+
+/*
+ * Memory layout of a batch of N images of C channels, H rows, W columns.
+ * Element (n, c, y, x) is at n*n_stride + c*c_stride + y*row_pitch + x*px_stride.
+ * Two layouts are accepted:
+ *   interleaved (NHWC / HWC): px_stride == C, c_stride == 1, C <= 4;
+ *   planar (NCHW):            px_stride == 1 (C planes of H x W each).
+ * For C == 1 both readings coincide. row_pitch >= W * px_stride.
+ */
+typedef struct {
+    int32_t N, C, H, W;
+    int64_t n_stride, c_stride, row_pitch, px_stride;
+} rs_layout;
+
+/* Tightly packed layouts: interleaved HWC (n_stride = H*W*C) and planar NCHW. */
+rs_layout rs_layout_hwc(int32_t N, int32_t H, int32_t W, int32_t C);
+rs_layout rs_layout_nchw(int32_t N, int32_t C, int32_t H, int32_t W);
+
+const char* rs_status_string(rs_status s);
+const char* rs_version(void);
+/* CUDA error code (cudaError_t) behind the calling thread's last RS_ERR_CUDA. */
+int rs_last_cuda_error(void);
+
+/*
+ * Diagnostic: synchronises `stream`, then reads and clears the current
+ * device's fault word. A kernel that finds an internal bound violated (a
+ * staged footprint larger than its shared-memory bound, a work index out of
+ * range) records a nonzero code there and skips the access instead of
+ * faulting. 0 means no kernel has reported anything since the last read.
+ */
+rs_status rs_debug_fault(void* stream, uint32_t* code);
+
+/*
+ * Resize one tightly packed HWC image (Sec. II.B, Eqs. 1-5): src is H x W x C
+ * of `dtype`, dst is Ho x Wo x C of the same dtype, 1 <= C <= 4. Asymmetric
+ * map (Eq. 1), a = -1/2, tiled kernel.
+ */
+rs_status rs_resize(const void* src, int H, int W, int C, rs_dtype dtype,
+                    void* dst, int Ho, int Wo, rs_method method, void* stream);
+
+/*
+ * General form: N images of any accepted layout (in / out must have the same
+ * N, C and layout kind; strides may differ). opt may be NULL (defaults).
+ */
+rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
+                       const rs_layout* out, rs_dtype dtype, rs_method method,
+                       const rs_options* opt, void* stream);
+
+/*
+ * Backward (adjoint) of rs_resize_ex for RS_F32: grad_in = A^T grad_out,
+ * where A is the linear map the forward applies (per axis, the transpose of
+ * the interpolation weights, summed over the clamped taps). Computed in
+ * gather form: every input sample sums, in a fixed order, the output
+ * samples whose taps name it, so results are deterministic (no atomics).
+ * grad_in is OVERWRITTEN. `workspace` is a device buffer of at least the
+ * size rs_resize_backward_workspace() reports (per-axis transposed weight
+ * tables); it is written by the call and may be reused after the call's
+ * work on `stream` has finished.
+ */
+rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in,
+                                       rs_method method, const rs_options* opt,
+                                       size_t* bytes);
+rs_status rs_resize_backward(const void* grad_out, const rs_layout* out,
+                             void* grad_in, const rs_layout* in, rs_dtype dtype,
+                             rs_method method, const rs_options* opt,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Ragged batch: n independent images, each with its own size, scale, channel
+ * count (interleaved, 1..4) and method, resampled by ONE persistent kernel
+ * launch that walks a work list of output tiles. Host array of descriptors;
+ * pitches in elements. All images share `dtype` and the options' coord and a.
+ */
+typedef struct {
+    const void* src;
+    void* dst;
+    int32_t H, W, C, Ho, Wo;
+    int32_t method;            /* rs_method */
+    int64_t src_pitch, dst_pitch;
+} rs_image_desc;
+
+/* Device workspace bytes rs_resize_batched needs for these descriptors. */
+rs_status rs_resize_batched_workspace(const rs_image_desc* d, int n, rs_dtype dtype,
+                                      size_t* bytes);
+/* Uploads the work list into `workspace` (async on `stream`) and launches. */
+rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype,
+                            void* workspace, size_t workspace_bytes,
+                            const rs_options* opt, void* stream);
+
+/*
+ * Replayable batch: the work list is uploaded once and the persistent launch
+ * is recorded as a CUDA graph; each rs_batched_plan_launch replays it on a
+ * stream. The plan refers to the descriptors' src / dst buffers and to
+ * `workspace`, which must stay valid until rs_batched_plan_destroy.
+ */
+typedef struct rs_batched_plan rs_batched_plan;
+rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype,
+                                 void* workspace, size_t workspace_bytes,
+                                 const rs_options* opt, void* stream,
+                                 rs_batched_plan** plan);
+rs_status rs_batched_plan_launch(rs_batched_plan* plan, void* stream);
+rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
+
+/*
+ * Autotuner. A tile configuration of the tiled kernel: tile_w output
+ * elements x tile_h output rows per thread block of `threads` threads.
+ * rs_autotune times every candidate configuration on the caller's buffers
+ * (dst is overwritten; the stream is synchronised while it runs) and stores
+ * the fastest in the in-process cache, keyed by GPU, dtype, method, channel
+ * layout and scale class; later RS_IMPL_AUTO calls with that key use it.
+ * The cache can be saved to and loaded from a text file.
+ */
+typedef struct {
+    int32_t tile_w, tile_h, threads;
+    float best_us;      /* measured time of the chosen configuration */
+    float default_us;   /* measured time of the default configuration */
+    int32_t candidates; /* number of configurations timed */
+} rs_tile_config;
+
+rs_status rs_autotune(const void* src, const rs_layout* in, void* dst,
+                      const rs_layout* out, rs_dtype dtype, rs_method method,
+                      const rs_options* opt, void* stream, rs_tile_config* best);
+rs_status rs_tune_cache_save(const char* path);
+rs_status rs_tune_cache_load(const char* path);
+void rs_tune_cache_clear(void);
+/* The configuration RS_IMPL_AUTO would use for this problem (cached or default). */
+rs_status rs_tile_config_for(const rs_layout* in, const rs_layout* out, rs_dtype dtype,
+                             rs_method method, const rs_options* opt, rs_tile_config* cfg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RESAMPLE_H */

@@ -1,0 +1,405 @@
+// Backward (adjoint) of the forward resampling, in gather form.
+//
+// The forward is a separable linear map: per plane Y = Ay X Ax^T, where row
+// j of an axis matrix holds output j's tap weights at the clamped source
+// indices. The gradient is dX = Ay^T dY Ax. Row i of A^T is sparse and
+// contiguous: since the first tap index of output j never decreases with j,
+// the outputs whose taps land on input i form one range [jlo(i), jhi(i)];
+// border inputs also receive the clamped taps, which only widens their range.
+//
+// 1. k_adjoint_table builds, per axis, jlo(i), the range length and the
+//    summed weights w(i, j) = sum over taps q of output j with
+//    clamp(first(j) + q) == i, into the caller's workspace.
+// 2. k_adjoint computes a tile of dX: it stages the dY footprint of the tile
+//    in shared memory, applies the x-axis transpose to every staged row, then
+//    the y-axis transpose, and writes dX. Every dX element is one fixed-order
+//    sum, so the result is deterministic (no atomics).
+#include <algorithm>
+#include <vector>
+
+#include "capi_internal.h"
+#include "rs_common.cuh"
+
+namespace rs {
+
+// Exact first tap index on the host (same integer arithmetic as the device).
+static int64_t host_floor_div(int64_t num, int64_t den)
+{
+    int64_t q = num / den;
+    if ((num % den != 0) && (num < 0)) q -= 1;
+    return q;
+}
+
+static int host_first_tap(int j, int n, int m, int method, int coord)
+{
+    if (method == M_NEAREST) {
+        if (coord == COORD_ASYMMETRIC) return (int)host_floor_div((int64_t)j * n, m);
+        return (int)host_floor_div((int64_t)(2 * j + 1) * n, 2 * (int64_t)m);
+    }
+    int64_t i0 = coord == COORD_ASYMMETRIC ? host_floor_div((int64_t)j * n, m)
+                                           : host_floor_div((int64_t)(2 * j + 1) * n - m, 2 * (int64_t)m);
+    return (int)(method == M_BICUBIC ? i0 - 1 : i0);
+}
+
+// Ranges [lo[i], hi[i]] of outputs touching input i (hi < lo when none).
+struct AxisRanges {
+    std::vector<int> lo, hi;
+    int kmax = 0;
+};
+
+static AxisRanges host_ranges(int n, int m, int method, int coord)
+{
+    const int KT = method_taps(method);
+    std::vector<int> first(m);
+    for (int j = 0; j < m; ++j) first[j] = host_first_tap(j, n, m, method, coord);
+    AxisRanges R;
+    R.lo.resize(n);
+    R.hi.resize(n);
+    for (int i = 0; i < n; ++i) {
+        // contributors: first(j) in [lo_i, hi_i] with the border widening
+        const int64_t lo_i = (i == 0) ? INT32_MIN : (int64_t)i - KT + 1;
+        const int64_t hi_i = (i == n - 1) ? INT32_MAX : (int64_t)i;
+        const int jl = (int)(std::lower_bound(first.begin(), first.end(), lo_i) - first.begin());
+        const int jh = (int)(std::upper_bound(first.begin(), first.end(), hi_i) - first.begin()) - 1;
+        R.lo[i] = jl;
+        R.hi[i] = jh;
+        R.kmax = std::max(R.kmax, jh - jl + 1);
+    }
+    return R;
+}
+
+__device__ __forceinline__ int first_tap_rt(int j, int n, int m, int method, int coord)
+{
+    if (method == M_NEAREST) return first_tap<1>(j, n, m, coord);
+    if (method == M_BILINEAR) return first_tap<2>(j, n, m, coord);
+    return first_tap<4>(j, n, m, coord);
+}
+
+__device__ __forceinline__ int taps_rt(int j, int n, int m, int method, int coord, float a, float* w)
+{
+    if (method == M_NEAREST) return taps<1>(j, n, m, coord, a, w);
+    if (method == M_BILINEAR) return taps<2>(j, n, m, coord, a, w);
+    return taps<4>(j, n, m, coord, a, w);
+}
+
+// One thread per input index i of an axis (n inputs, m outputs).
+__global__ void k_adjoint_table(int n, int m, int method, int coord, float a, int* lo_out, int* cnt_out,
+                                float* w_out, int K, unsigned int* fault)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int KT = method == M_NEAREST ? 1 : method == M_BILINEAR ? 2 : 4;
+    // jlo = first j with first(j) >= i - KT + 1 (0 for i == 0)
+    int jl = 0;
+    if (i > 0) {
+        int l = 0, h = m;
+        while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (first_tap_rt(mid, n, m, method, coord) >= i - KT + 1) h = mid; else l = mid + 1;
+        }
+        jl = l;
+    }
+    // jhi = last j with first(j) <= i (m - 1 for i == n - 1)
+    int jh = m - 1;
+    if (i < n - 1) {
+        int l = 0, h = m;
+        while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (first_tap_rt(mid, n, m, method, coord) > i) h = mid; else l = mid + 1;
+        }
+        jh = l - 1;
+    }
+    int cnt = max(0, jh - jl + 1);
+    if (cnt > K) {
+        report_fault(fault, FAULT_BWD_TAPS);
+        cnt = K;
+    }
+    lo_out[i] = jl;
+    cnt_out[i] = cnt;
+    for (int k = 0; k < K; ++k) {
+        float acc = 0.0f;
+        if (k < cnt) {
+            float w[4];
+            const int f = taps_rt(jl + k, n, m, method, coord, a, w);
+            for (int q = 0; q < KT; ++q)
+                if (clampi(f + q, n) == i) acc += w[q];
+        }
+        w_out[(int64_t)i * K + k] = acc;
+    }
+}
+
+struct AdjTables {
+    const int *ylo, *ycnt, *xlo, *xcnt;
+    const float *yw, *xw;
+    int yK, xK;
+};
+
+struct AdjCfg {
+    int tile_w, tile_h, ty;   // dX elements per tile row (= blockDim.x), dX rows per tile, blockDim.y
+    int fh_max, fwe_max;      // staged dY footprint bound
+    size_t smem;
+};
+
+// g describes the FORWARD problem: H x W inputs (dX), Ho x Wo outputs (dY).
+template <int KX, int C>
+__global__ void __launch_bounds__(256)
+k_adjoint(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, const AdjTables tb,
+          const AdjCfg cfg, unsigned int* fault)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int tx = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
+    const int tid = ty * blockDim.x + tx, nthreads = blockDim.x * TY;
+    const int TWE = cfg.tile_w, TH = cfg.tile_h;
+    const int plane = blockIdx.z;
+    const float* s = dY + g.dp.offset(plane);   // dY has the output layout
+    float* d = dX + g.sp.offset(plane);
+
+    const int64_t WC = (int64_t)g.W * C;
+    const int64_t e0 = (int64_t)blockIdx.x * TWE;
+    const int i0 = blockIdx.y * TH;
+    const int nE = (int)min((int64_t)TWE, WC - e0);
+    const int nR = min(TH, g.H - i0);
+    const int x_first = (int)(e0 / C), x_last = (int)((e0 + nE - 1) / C);
+
+    // Footprint in dY (ranges are monotone; empty ranges have cnt 0).
+    int r_lo = tb.ylo[i0], r_hi = tb.ylo[i0 + nR - 1] + tb.ycnt[i0 + nR - 1] - 1;
+    int c_lo = tb.xlo[x_first], c_hi = tb.xlo[x_last] + tb.xcnt[x_last] - 1;
+    r_hi = max(r_hi, r_lo);     // keep at least one staged row / column
+    c_hi = max(c_hi, c_lo);
+    r_lo = min(r_lo, g.Ho - 1);
+    r_hi = min(r_hi, g.Ho - 1);
+    c_lo = min(c_lo, g.Wo - 1);
+    c_hi = min(c_hi, g.Wo - 1);
+    const int FH = r_hi - r_lo + 1, FWE = (c_hi - c_lo + 1) * C;
+    if (FH > cfg.fh_max || FWE > cfg.fwe_max) {
+        if (tid == 0) report_fault(fault, FAULT_BWD_SPAN);
+        return;
+    }
+    float* S = sm;                                  // [fh_max][fwe_max]
+    float* Hb = S + cfg.fh_max * cfg.fwe_max;       // [fh_max][TWE]
+    float* RW = Hb + cfg.fh_max * TWE;              // [TH][yK]
+    int* RL = reinterpret_cast<int*>(RW + TH * tb.yK);   // [TH] first staged row
+    int* RC = RL + TH;                                   // [TH] count
+
+    for (int i = tid; i < nR; i += nthreads) {
+        RL[i] = tb.ylo[i0 + i] - r_lo;
+        RC[i] = tb.ycnt[i0 + i];
+        for (int k = 0; k < tb.yK; ++k) RW[i * tb.yK + k] = tb.yw[(int64_t)(i0 + i) * tb.yK + k];
+    }
+    // this thread's dX element: its x-axis range and weights
+    const bool active = tx < nE;
+    int xoff = 0, xcnt = 0;
+    float wx[KX];
+    #pragma unroll
+    for (int k = 0; k < KX; ++k) wx[k] = 0.0f;
+    if (active) {
+        const int64_t e = e0 + tx;
+        const int x = (int)(e / C), c = (int)(e - (int64_t)x * C);
+        xoff = (tb.xlo[x] - c_lo) * C + c;
+        xcnt = min(tb.xcnt[x], KX);
+        #pragma unroll
+        for (int k = 0; k < KX; ++k)
+            if (k < xcnt) wx[k] = tb.xw[(int64_t)x * tb.xK + k];
+    }
+    // stage the dY footprint
+    for (int r = tid / 32; r < FH; r += nthreads / 32) {
+        const float* srow = s + (int64_t)(r_lo + r) * g.dst_pitch + (int64_t)c_lo * C;
+        float* Sr = S + r * cfg.fwe_max;
+        for (int ce = tid % 32; ce < FWE; ce += 32) Sr[ce] = __ldg(srow + ce);
+    }
+    __syncthreads();
+    // x-axis transpose of every staged row
+    if (active) {
+        for (int r = ty; r < FH; r += TY) {
+            const float* Sr = S + r * cfg.fwe_max + xoff;
+            float acc = 0.0f;
+            #pragma unroll
+            for (int k = 0; k < KX; ++k)
+                if (k < xcnt) acc = fmaf(wx[k], Sr[k * C], acc);
+            Hb[r * TWE + tx] = acc;
+        }
+    }
+    __syncthreads();
+    // y-axis transpose and store
+    if (active) {
+        for (int i = ty; i < nR; i += TY) {
+            const int b = RL[i], cnt = RC[i];
+            const float* w = RW + i * tb.yK;
+            float acc = 0.0f;
+            for (int k = 0; k < cnt; ++k) acc = fmaf(w[k], Hb[(b + k) * TWE + tx], acc);
+            d[(int64_t)(i0 + i) * g.src_pitch + e0 + tx] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct BwdPlan {
+    AxisRanges ry, rx;
+    int yK, xK;
+    size_t ws_bytes;
+    size_t off_ylo, off_ycnt, off_yw, off_xlo, off_xcnt, off_xw;
+};
+
+static BwdPlan plan_tables(const Geom& g, int method)
+{
+    BwdPlan p;
+    p.ry = host_ranges(g.H, g.Ho, method, g.coord);
+    p.rx = host_ranges(g.W, g.Wo, method, g.coord);
+    p.yK = std::max(1, p.ry.kmax);
+    p.xK = std::max(1, p.rx.kmax);
+    size_t o = 0;
+    p.off_ylo = o; o = align256(o + sizeof(int) * g.H);
+    p.off_ycnt = o; o = align256(o + sizeof(int) * g.H);
+    p.off_yw = o; o = align256(o + sizeof(float) * (size_t)g.H * p.yK);
+    p.off_xlo = o; o = align256(o + sizeof(int) * g.W);
+    p.off_xcnt = o; o = align256(o + sizeof(int) * g.W);
+    p.off_xw = o; o = align256(o + sizeof(float) * (size_t)g.W * p.xK);
+    p.ws_bytes = o;
+    return p;
+}
+
+// Largest staged footprint over all tiles of `tile` destination indices
+// (rows: tile = TH; columns: element tiles of TWE over C channels).
+static int footprint_bound(const AxisRanges& R, int n, int tile, int C, int m)
+{
+    int best = 1;
+    const int64_t total = (int64_t)n * C;
+    for (int64_t e0 = 0; e0 < total; e0 += tile) {
+        const int first = (int)(e0 / C);
+        const int last = (int)(std::min(total, e0 + tile) - 1) / C;
+        int lo = R.lo[first], hi = R.hi[last];
+        hi = std::max(hi, lo);
+        lo = std::min(lo, m - 1);
+        hi = std::min(hi, m - 1);
+        best = std::max(best, hi - lo + 1);
+    }
+    return best;
+}
+
+static bool adj_config(const Geom& g, const BwdPlan& p, int TH, AdjCfg& cfg)
+{
+    cfg.tile_w = 128;
+    cfg.ty = 2;
+    cfg.tile_h = TH;
+    cfg.fh_max = footprint_bound(p.ry, g.H, TH, 1, g.Ho);
+    cfg.fwe_max = (footprint_bound(p.rx, g.W, cfg.tile_w, g.C, g.Wo) * g.C + 3) & ~3;
+    cfg.smem = sizeof(float) * ((size_t)cfg.fh_max * cfg.fwe_max + (size_t)cfg.fh_max * cfg.tile_w +
+                                (size_t)TH * p.yK) + sizeof(int) * 2 * (size_t)TH;
+    return cfg.smem <= max_smem_per_block();
+}
+
+template <int KX, int C>
+static cudaError_t launch_adj(const Geom& g, const float* dY, float* dX, const AdjTables& tb, const AdjCfg& cfg,
+                              cudaStream_t st)
+{
+    auto kern = k_adjoint<KX, C>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    dim3 block(cfg.tile_w, cfg.ty);
+    dim3 grid((unsigned)(((int64_t)g.W * C + cfg.tile_w - 1) / cfg.tile_w), (unsigned)((g.H + cfg.tile_h - 1) / cfg.tile_h),
+              (unsigned)g.planes);
+    kern<<<grid, block, cfg.smem, st>>>(g, dY, dX, tb, cfg, fault_word());
+    return cudaGetLastError();
+}
+
+template <int KX>
+static cudaError_t launch_adj_c(const Geom& g, const float* dY, float* dX, const AdjTables& tb, const AdjCfg& cfg,
+                                cudaStream_t st)
+{
+    switch (g.C) {
+    case 1: return launch_adj<KX, 1>(g, dY, dX, tb, cfg, st);
+    case 2: return launch_adj<KX, 2>(g, dY, dX, tb, cfg, st);
+    case 3: return launch_adj<KX, 3>(g, dY, dX, tb, cfg, st);
+    case 4: return launch_adj<KX, 4>(g, dY, dX, tb, cfg, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+static rs_status bwd_geom(const rs_layout* out, const rs_layout* in, rs_method method, const rs_options& o,
+                          Geom& g)
+{
+    LayoutInfo li, lo;
+    // The forward's input layout is `in` (dX) and its output layout is `out` (dY).
+    return geom_from_layouts(in, out, RS_F32, method, o, g, li, lo);
+}
+
+extern "C" {
+
+rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in, rs_method method,
+                                       const rs_options* opt, size_t* bytes)
+{
+    if (!bytes) return RS_ERR_INVALID_ARG;
+    const rs_options o = options_or_default(opt);
+    Geom g;
+    rs_status s = bwd_geom(out, in, method, o, g);
+    if (s != RS_OK) return s;
+    *bytes = plan_tables(g, method).ws_bytes;
+    return RS_OK;
+}
+
+rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* grad_in, const rs_layout* in,
+                             rs_dtype dtype, rs_method method, const rs_options* opt, void* workspace,
+                             size_t workspace_bytes, void* stream)
+{
+    if (dtype != RS_F32) return RS_ERR_UNSUPPORTED;
+    const rs_options o = options_or_default(opt);
+    Geom g;
+    // make_geom checks pointers, alignment and overlap with src = dX, dst = dY.
+    rs_status s = make_geom(grad_in, in, grad_out, out, RS_F32, method, o, g);
+    if (s != RS_OK) return s;
+    BwdPlan p = plan_tables(g, method);
+    if (!workspace || workspace_bytes < p.ws_bytes) return RS_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return RS_ERR_ALIGNMENT;
+    {
+        LayoutInfo li, lo;
+        classify(in, li);
+        classify(out, lo);
+        char* ws = static_cast<char*>(workspace);
+        if (overlaps(ws, (int64_t)p.ws_bytes, grad_in, li.extent * 4) ||
+            overlaps(ws, (int64_t)p.ws_bytes, grad_out, lo.extent * 4))
+            return RS_ERR_INVALID_ARG;
+    }
+    const int KX = p.xK;
+    if (KX > 64) return RS_ERR_UNSUPPORTED;   // > 16x upscale along x
+    AdjCfg cfg;
+    bool ok = false;
+    for (int TH = 32; TH >= 1 && !ok; TH >>= 1) ok = adj_config(g, p, TH, cfg);
+    if (!ok) return RS_ERR_UNSUPPORTED;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    AdjTables tb;
+    tb.ylo = reinterpret_cast<int*>(ws + p.off_ylo);
+    tb.ycnt = reinterpret_cast<int*>(ws + p.off_ycnt);
+    tb.yw = reinterpret_cast<float*>(ws + p.off_yw);
+    tb.xlo = reinterpret_cast<int*>(ws + p.off_xlo);
+    tb.xcnt = reinterpret_cast<int*>(ws + p.off_xcnt);
+    tb.xw = reinterpret_cast<float*>(ws + p.off_xw);
+    tb.yK = p.yK;
+    tb.xK = p.xK;
+    unsigned int* fw = fault_word();
+    k_adjoint_table<<<(g.H + 127) / 128, 128, 0, st>>>(g.H, g.Ho, method, g.coord, g.a, (int*)tb.ylo,
+                                                        (int*)tb.ycnt, (float*)tb.yw, tb.yK, fw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    k_adjoint_table<<<(g.W + 127) / 128, 128, 0, st>>>(g.W, g.Wo, method, g.coord, g.a, (int*)tb.xlo,
+                                                        (int*)tb.xcnt, (float*)tb.xw, tb.xK, fw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    const float* dY = static_cast<const float*>(grad_out);
+    float* dX = static_cast<float*>(grad_in);
+    if (KX <= 4) e = launch_adj_c<4>(g, dY, dX, tb, cfg, st);
+    else if (KX <= 8) e = launch_adj_c<8>(g, dY, dX, tb, cfg, st);
+    else if (KX <= 16) e = launch_adj_c<16>(g, dY, dX, tb, cfg, st);
+    else if (KX <= 32) e = launch_adj_c<32>(g, dY, dX, tb, cfg, st);
+    else e = launch_adj_c<64>(g, dY, dX, tb, cfg, st);
+    return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,31 @@
+// Host-side helpers shared by the C ABI translation units.
+#pragma once
+
+#include "../../include/resample.h"
+#include "rs_internal.h"
+
+namespace rs {
+
+struct LayoutInfo {
+    int kind;        // 0 interleaved, 1 planar
+    int ci, cp;      // interleaved channels, planes per image
+    int64_t extent;  // elements from the base pointer to one past the last element
+};
+
+rs_status cuda_status(cudaError_t e);
+rs_options options_or_default(const rs_options* opt);
+rs_status check_options(const rs_options& o, int method);
+rs_status classify(const rs_layout* L, LayoutInfo& info);
+bool overlaps(const void* a, int64_t abytes, const void* b, int64_t bbytes);
+rs_status geom_from_layouts(const rs_layout* in, const rs_layout* out, int dtype, int method,
+                            const rs_options& o, Geom& g, LayoutInfo& li, LayoutInfo& lo);
+rs_status make_geom(const void* src, const rs_layout* in, const void* dst, const rs_layout* out,
+                    int dtype, int method, const rs_options& o, Geom& g);
+
+// Tile configuration for a forward call: explicit options, else the tuning
+// cache, else the default.
+rs_status choose_tile(const Geom& g, int method, int dtype, const rs_options& o, TileCfg& cfg);
+
+cudaError_t read_fault(cudaStream_t st, unsigned int* code);
+
+}  // namespace rs

@@ -1,0 +1,93 @@
+// Per-device state of the library: the fault word and cached device limits.
+// The fault word is a static __device__ variable; host code must not use its
+// name as a device address, so its address is resolved per device with
+// cudaGetSymbolAddress (with that device current) and passed to kernels.
+#include <mutex>
+
+#include "rs_internal.h"
+
+namespace rs {
+
+static __device__ unsigned int g_fault_word;
+
+static constexpr int kMaxDevices = 64;
+static std::mutex g_mu;
+static unsigned int* g_fault_ptr[kMaxDevices];
+static size_t g_smem[kMaxDevices];
+static int g_sms[kMaxDevices];
+
+static int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+unsigned int* fault_word()
+{
+    const int dev = current_device();
+    if (dev < 0) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_fault_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_fault_word) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        g_fault_ptr[dev] = static_cast<unsigned int*>(p);
+    }
+    return g_fault_ptr[dev];
+}
+
+size_t max_smem_per_block()
+{
+    const int dev = current_device();
+    if (dev < 0) return 48 * 1024;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_smem[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+            v = 48 * 1024;
+        g_smem[dev] = (size_t)v;
+    }
+    return g_smem[dev];
+}
+
+int num_sms()
+{
+    const int dev = current_device();
+    if (dev < 0) return 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        g_sms[dev] = v;
+    }
+    return g_sms[dev];
+}
+
+int method_taps(int method)
+{
+    return method == M_NEAREST ? 1 : method == M_BILINEAR ? 2 : 4;
+}
+
+size_t dtype_size(int dtype)
+{
+    return dtype == DT_U8 ? 1 : dtype == DT_F32 ? 4 : 2;
+}
+
+// Reads and clears the current device's fault word after synchronising `st`.
+cudaError_t read_fault(cudaStream_t st, unsigned int* code)
+{
+    unsigned int* fw = fault_word();
+    *code = 0;
+    if (!fw) return cudaErrorInvalidSymbol;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(code, fw, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    const unsigned int zero = 0;
+    return cudaMemcpy(fw, &zero, sizeof(unsigned int), cudaMemcpyHostToDevice);
+}
+
+}  // namespace rs

@@ -1,0 +1,79 @@
+// Internal host/device interface of libresample: problem geometry, tile
+// configurations and the kernel launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rs {
+
+enum { COORD_ASYMMETRIC = 0, COORD_HALF_PIXEL = 1 };
+enum { DT_U8 = 0, DT_F16 = 1, DT_BF16 = 2, DT_F32 = 3 };
+enum { M_NEAREST = 0, M_BILINEAR = 1, M_BICUBIC = 2 };
+
+// Fault codes recorded in the device fault word.
+enum : unsigned int {
+    FAULT_NONE = 0,
+    FAULT_TILE_SRC_SPAN = 0x101,   // staged source footprint exceeds the smem bound
+    FAULT_BWD_SPAN = 0x201,        // backward footprint exceeds the smem bound
+    FAULT_BWD_TAPS = 0x202,        // transposed tap count exceeds the table width
+    FAULT_BATCH_SPAN = 0x301,      // batched tile footprint exceeds the smem bound
+    FAULT_BATCH_INDEX = 0x302,     // batched work index out of range
+};
+
+// Addressing of plane p (0 <= p < N * cp) of a batch: planar layouts have cp
+// planes per image, interleaved layouts cp = 1.
+struct PlaneMap {
+    int64_t n_stride, c_stride;
+    int cp;
+#ifdef __CUDACC__
+    __host__ __device__ __forceinline__ int64_t offset(int p) const
+    {
+        return (int64_t)(p / cp) * n_stride + (int64_t)(p % cp) * c_stride;
+    }
+#endif
+};
+
+// One resampling problem: `planes` images of H x W pixels with C interleaved
+// channels (C = 1 for planar data), row pitches in elements.
+struct Geom {
+    int H, W, Ho, Wo, C;
+    int64_t src_pitch, dst_pitch;
+    PlaneMap sp, dp;
+    int planes;
+    int coord;
+    float a;
+};
+
+// Tile configuration of the tiled forward kernel: tile_w output elements
+// (multiple of 4) x tile_h output rows per block of `threads` threads;
+// sh_max x swe_max bounds the staged source footprint.
+struct TileCfg {
+    int tile_w, tile_h, threads;
+    int sh_max, swe_max;
+    size_t smem;
+};
+
+int method_taps(int method);
+size_t dtype_size(int dtype);
+
+// Maximum dynamic shared memory a block may use on this device.
+size_t max_smem_per_block();
+int num_sms();
+
+// Fault word of the current device (a static __device__ word resolved by
+// cudaGetSymbolAddress), or nullptr if it cannot be resolved.
+unsigned int* fault_word();
+
+// Completes cfg (sh_max, swe_max, smem) for the problem; false if the
+// configuration is malformed or does not fit in shared memory.
+bool tiled_config(const Geom& g, int method, TileCfg& cfg);
+TileCfg tiled_default(const Geom& g, int method);
+
+cudaError_t launch_tiled(const Geom& g, int method, int dtype, const void* src, void* dst,
+                         const TileCfg& cfg, cudaStream_t st);
+cudaError_t launch_plain(const Geom& g, int method, int dtype, const void* src, void* dst,
+                         int bw, int bh, cudaStream_t st);
+
+}  // namespace rs

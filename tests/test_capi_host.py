@@ -1,0 +1,128 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every function include/resample.h declares, and its host-side
+argument validation rejects bad calls before touching CUDA."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "resample.h"
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1001_1718_gb300 import build as b
+    b.build()
+    from paper_1001_1718_gb300 import _binding
+    return _binding.lib()
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(rs_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rs_resize", "rs_resize_ex", "rs_resize_backward", "rs_resize_batched",
+                     "rs_autotune", "rs_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_1001_1718_gb300 import _binding
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each
+    assert set(declared_functions()) <= set(_binding.SIGNATURES)
+
+
+def test_status_strings_and_defaults(L):
+    from paper_1001_1718_gb300 import _binding as B
+    assert L.rs_status_string(0) == b"ok"
+    assert L.rs_status_string(4).startswith(b"workspace")
+    o = B.options()
+    assert (o.coord, o.cubic_a, o.impl, o.tile_w, o.tile_h, o.threads) == (0, -0.5, 0, 0, 0, 0)
+    lay = L.rs_layout_hwc(2, 5, 7, 3)
+    assert (lay.N, lay.C, lay.H, lay.W, lay.px_stride, lay.c_stride, lay.row_pitch, lay.n_stride) == \
+        (2, 3, 5, 7, 3, 1, 21, 105)
+    lay = L.rs_layout_nchw(2, 3, 5, 7)
+    assert (lay.px_stride, lay.row_pitch, lay.c_stride, lay.n_stride) == (1, 7, 35, 105)
+
+
+def test_validation_rejects_before_any_launch(L):
+    """Each call below fails host validation, so no CUDA call is made."""
+    from paper_1001_1718_gb300 import _binding as B
+    P = 0x10000  # never dereferenced: validation fails first
+    Q = 0x90000000
+    # null pointers
+    assert L.rs_resize(None, 4, 4, 1, B.RS_U8, Q, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+    assert L.rs_resize(P, 4, 4, 1, B.RS_U8, None, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+    # sizes out of range
+    for H, W, Ho, Wo in ((0, 4, 8, 8), (4, 4, 0, 8), (70000, 4, 8, 8), (4, 4, 8, 65536), (-3, 4, 8, 8)):
+        assert L.rs_resize(P, H, W, 1, B.RS_U8, Q, Ho, Wo, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+    # channels, dtype, method
+    assert L.rs_resize(P, 4, 4, 5, B.RS_U8, Q, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+    assert L.rs_resize(P, 4, 4, 1, 7, Q, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+    assert L.rs_resize(P, 4, 4, 1, B.RS_U8, Q, 8, 8, 9, None) == B.RS_ERR_INVALID_ARG
+    # misaligned FP32 pointer
+    assert L.rs_resize(P + 2, 4, 4, 1, B.RS_F32, Q, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_ALIGNMENT
+    # overlapping source and destination
+    assert L.rs_resize(P, 16, 16, 1, B.RS_U8, P + 100, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
+
+
+def test_layout_validation(L):
+    from paper_1001_1718_gb300 import _binding as B
+    P, Q = 0x10000, 0x90000000
+    good_in = L.rs_layout_nchw(2, 3, 8, 8)
+    good_out = L.rs_layout_nchw(2, 3, 16, 16)
+    o = B.options(coord=5)
+    assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_F32, 1,
+                          ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
+    o = B.options(cubic_a=float("nan"))
+    assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_F32, 2,
+                          ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
+    bad = L.rs_layout_nchw(2, 3, 8, 8)
+    bad.row_pitch = 4                 # shorter than a row
+    assert L.rs_resize_ex(P, ctypes.byref(bad), Q, ctypes.byref(good_out), B.RS_F32, 1,
+                          None, None) == B.RS_ERR_INVALID_ARG
+    bad = L.rs_layout_nchw(2, 3, 8, 8)
+    bad.c_stride = 10                 # planes overlap
+    assert L.rs_resize_ex(P, ctypes.byref(bad), Q, ctypes.byref(good_out), B.RS_F32, 1,
+                          None, None) == B.RS_ERR_INVALID_ARG
+    mismatch = L.rs_layout_nchw(1, 3, 16, 16)   # N differs
+    assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(mismatch), B.RS_F32, 1,
+                          None, None) == B.RS_ERR_INVALID_ARG
+    hwc5 = L.rs_layout_hwc(1, 8, 8, 5)
+    assert L.rs_resize_ex(P, ctypes.byref(hwc5), Q, ctypes.byref(L.rs_layout_hwc(1, 4, 4, 5)),
+                          B.RS_U8, 1, None, None) == B.RS_ERR_UNSUPPORTED
+    # plain kernel block too large
+    o = B.options(impl=B.RS_IMPL_PLAIN, tile_w=64, tile_h=32)
+    assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_F32, 1,
+                          ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
+
+
+def test_tune_cache_file_roundtrip(L, tmp_path):
+    p = tmp_path / "tune.txt"
+    p.write_text("# resample-tune v1\nsms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27 512 16 256\nbogus line\n")
+    assert L.rs_tune_cache_load(str(p).encode()) == 0
+    q = tmp_path / "out.txt"
+    assert L.rs_tune_cache_save(str(q).encode()) == 0
+    assert "sms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27 512 16 256" in q.read_text()
+    stale = tmp_path / "stale.txt"
+    stale.write_text("key 1 2 3\n")   # no version header: ignored
+    assert L.rs_tune_cache_load(str(stale).encode()) != 0
+    L.rs_tune_cache_clear()
+    assert L.rs_tune_cache_save(str(q).encode()) == 0
+    assert q.read_text().strip() == "# resample-tune v1"
+
+
+def test_product_path_refuses_cpu_tensors():
+    import torch
+    import paper_1001_1718_gb300 as rs
+    with pytest.raises(ValueError):
+        rs.resize(torch.zeros(4, 4, 3, dtype=torch.uint8), (8, 8), "bilinear")

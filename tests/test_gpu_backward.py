@@ -1,0 +1,133 @@
+"""GPU backward parity: the gather-form adjoint kernel against the FP64
+oracle's adjoint (a scatter over the forward's taps), finite differences of
+the oracle forward, autograd plumbing and determinism."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+MN = {0: "nearest", 1: "bilinear", 2: "bicubic"}
+CN = {0: "asymmetric", 1: "half_pixel"}
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1718_gb300 as rs
+    return rs
+
+
+def _tol(oracle, H, W, Ho, Wo, method, coord, gmax):
+    """Normwise FP32 bound: 1e-5 * max|dY| * ||Ay^T||_inf * ||Ax^T||_inf."""
+    Ay = oracle.axis_matrix(H, Ho, method, coord)
+    Ax = oracle.axis_matrix(W, Wo, method, coord)
+    return 1e-5 * max(1.0, gmax) * np.abs(Ay.T).sum(1).max() * np.abs(Ax.T).sum(1).max()
+
+
+SHAPES = [(37, 53, 74, 106), (64, 48, 32, 24), (31, 29, 53, 71), (40, 40, 40, 40), (1, 17, 3, 40),
+          (23, 1, 9, 4), (300, 257, 600, 514), (120, 90, 17, 13)]
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("coord", [0, 1])
+def test_adjoint_nchw_matches_oracle(rs, oracle, method, coord):
+    for k, (H, W, Ho, Wo) in enumerate(SHAPES):
+        g = np.random.default_rng(100 + k).standard_normal((2, 3, Ho, Wo)).astype(np.float32)
+        gt = torch.from_numpy(g).cuda()
+        gi = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord])
+        torch.cuda.synchronize()
+        ref = oracle.adjoint_nchw(g.astype(np.float64), H, W, method, coord)
+        err = np.abs(gi.cpu().numpy().astype(np.float64) - ref).max()
+        tol = _tol(oracle, H, W, Ho, Wo, method, coord, np.abs(g).max())
+        assert err <= tol, f"{MN[method]} {CN[coord]} {H}x{W}<-{Ho}x{Wo}: {err} > {tol}"
+    assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("C", [1, 3, 4])
+def test_adjoint_hwc_matches_oracle(rs, oracle, C):
+    for method in (1, 2):
+        H, W, Ho, Wo = 45, 61, 97, 130
+        g = np.random.default_rng(7).standard_normal((Ho, Wo, C)).astype(np.float32)
+        gi = rs.resize_backward(torch.from_numpy(g).cuda(), (H, W), MN[method], layout="hwc")
+        torch.cuda.synchronize()
+        ref = oracle.adjoint(g.astype(np.float64), H, W, method)
+        tol = _tol(oracle, H, W, Ho, Wo, method, 0, np.abs(g).max())
+        assert np.abs(gi.cpu().numpy() - ref).max() <= tol
+
+
+def test_deterministic(rs):
+    g = torch.randn(4, 3, 300, 400, device="cuda")
+    a = rs.resize_backward(g, (150, 200), "bicubic")
+    b = rs.resize_backward(g, (150, 200), "bicubic")
+    c = rs.resize_backward(g, (150, 200), "bicubic")
+    assert torch.equal(a, b) and torch.equal(b, c)
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_autograd_function(rs, method):
+    x = torch.randn(2, 3, 40, 50, device="cuda", requires_grad=True)
+    y = rs.ResizeFn.apply(x, (80, 100), MN[method], "half_pixel", -0.5)
+    g = torch.randn_like(y)
+    y.backward(g)
+    ref = rs.resize_backward(g, (40, 50), MN[method], coord="half_pixel")
+    assert torch.equal(x.grad, ref)
+    # forward through the Function equals resize()
+    assert torch.equal(y.detach(), rs.resize(x.detach(), (80, 100), MN[method], layout="nchw", coord="half_pixel"))
+
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("scale", [2.0, 0.5])
+def test_against_central_differences(rs, oracle, method, coord, scale):
+    """dL/dx of L = <resize(x), g> by FP64 central differences (eps = 1e-6)
+    of the oracle forward on a 64x64 crop, at sampled input pixels."""
+    H = W = 64
+    Ho = Wo = int(64 * scale)
+    r = np.random.default_rng(21)
+    x = r.standard_normal((H, W))
+    g = r.standard_normal((Ho, Wo)).astype(np.float32)
+    gi = rs.resize_backward(torch.from_numpy(g).cuda(), (H, W), MN[method], coord=CN[coord])
+    gi = gi.cpu().numpy()
+    g64 = g.astype(np.float64)
+    for (i, j) in [(0, 0), (63, 63), (0, 31), (17, 5), (40, 62), (33, 33)]:
+        xp, xm = x.copy(), x.copy()
+        xp[i, j] += 1e-6
+        xm[i, j] -= 1e-6
+        fd = (np.sum(oracle.resize(xp, Ho, Wo, method, coord)[:, :, 0] * g64) -
+              np.sum(oracle.resize(xm, Ho, Wo, method, coord)[:, :, 0] * g64)) / 2e-6
+        assert abs(gi[i, j] - fd) < 1e-4 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("scale", [2.0, 0.5])
+def test_full_size_planes(rs, oracle, method, scale):
+    """Full size 32x3x512x512 backward; two planes checked against the oracle."""
+    H = W = 512
+    Ho = Wo = int(512 * scale)
+    g = torch.randn(32, 3, Ho, Wo, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    gi = rs.resize_backward(g, (H, W), MN[method])
+    torch.cuda.synchronize()
+    for (n, c) in ((0, 0), (31, 2)):
+        gp = g[n, c].cpu().numpy().astype(np.float64)
+        ref = oracle.adjoint(gp, H, W, method)[:, :, 0]
+        tol = _tol(oracle, H, W, Ho, Wo, method, 0, np.abs(gp).max())
+        assert np.abs(gi[n, c].cpu().numpy() - ref).max() <= tol
+    assert rs.debug_fault() == 0
+
+
+def test_workspace_errors(rs):
+    import ctypes
+    from paper_1001_1718_gb300 import _binding as B
+    g = torch.randn(1, 1, 20, 20, device="cuda")
+    x = torch.empty(1, 1, 10, 10, device="cuda")
+    Lo, Li = rs._layout(g, "nchw"), rs._layout(x, "nchw")
+    o = B.options()
+    st = torch.cuda.current_stream().cuda_stream
+    s = B.lib().rs_resize_backward(g.data_ptr(), ctypes.byref(Lo), x.data_ptr(), ctypes.byref(Li), B.RS_F32, 1,
+                                   ctypes.byref(o), None, 0, st)
+    assert s == B.RS_ERR_WORKSPACE
+    s = B.lib().rs_resize_backward(g.data_ptr(), ctypes.byref(Lo), x.data_ptr(), ctypes.byref(Li), B.RS_U8, 1,
+                                   ctypes.byref(o), None, 0, st)
+    assert s == B.RS_ERR_UNSUPPORTED

@@ -1,0 +1,111 @@
+"""GPU batched path: one persistent launch over ragged images of different
+sizes, scales, channel counts and methods, against the FP64 oracle and
+against per-image launches (bit for bit: the per-element arithmetic does
+not depend on the tiling); the replayable graph plan; the full 256-image
+workload on sampled points."""
+import numpy as np
+import pytest
+import torch
+
+from _parity import check
+
+pytestmark = pytest.mark.gpu
+MN = {0: "nearest", 1: "bilinear", 2: "bicubic"}
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1718_gb300 as rs
+    return rs
+
+
+def _batch(seed, n, dtype=torch.uint8):
+    r = np.random.default_rng(seed)
+    srcs, sizes, methods, host = [], [], [], []
+    for k in range(n):
+        H, W = int(r.integers(5, 300)), int(r.integers(5, 300))
+        C = int(r.choice([1, 3, 4]))
+        s = float(r.uniform(0.5, 4.0))
+        Ho, Wo = max(1, int(H * s)), max(1, int(W * s * r.uniform(0.8, 1.25)))
+        if dtype == torch.uint8:
+            x = r.integers(0, 256, (H, W, C)).astype(np.uint8)
+        else:
+            x = r.standard_normal((H, W, C)).astype(np.float32)
+        host.append(x)
+        srcs.append(torch.from_numpy(x).cuda())
+        sizes.append((Ho, Wo))
+        methods.append(MN[k % 3])
+    return srcs, sizes, methods, host
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float32])
+def test_batched_matches_oracle_and_single(rs, oracle, dtype):
+    srcs, sizes, methods, host = _batch(3, 24, dtype)
+    outs = rs.resize_batched(srcs, sizes, methods)
+    torch.cuda.synchronize()
+    dn = "u8" if dtype == torch.uint8 else "f32"
+    for x, s, m, y, h in zip(srcs, sizes, methods, outs, host):
+        single = rs.resize(x, s, m)
+        assert torch.equal(single, y)
+        code = rs.METHODS[m]
+        check(y, oracle.resize(h.astype(np.float64), s[0], s[1], code), dn, code,
+              float(np.abs(h).max()), f"batched {m} {h.shape}->{s}")
+    assert rs.debug_fault() == 0
+
+
+def test_plan_replay(rs):
+    srcs, sizes, methods, _ = _batch(4, 16)
+    outs = [torch.zeros((h, w, x.shape[2]), dtype=torch.uint8, device="cuda") for x, (h, w) in zip(srcs, sizes)]
+    plan = rs.BatchedPlan(srcs, outs, methods)
+    plan.launch()
+    torch.cuda.synchronize()
+    ref = [rs.resize(x, s, m) for x, s, m in zip(srcs, sizes, methods)]
+    assert all(torch.equal(a, b) for a, b in zip(outs, ref))
+    # the graph reads the same buffers: new input pixels give new outputs
+    for x in srcs:
+        x.copy_(255 - x)
+    for o in outs:
+        o.zero_()
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    ref = [rs.resize(x, s, m) for x, s, m in zip(srcs, sizes, methods)]
+    assert all(torch.equal(a, b) for a, b in zip(outs, ref))
+    plan.close()
+
+
+def test_pitched_images_and_invalid(rs):
+    x = torch.randint(0, 256, (50, 70 * 3 + 5), dtype=torch.uint8, device="cuda")
+    src = x[:, :210].view(50, 70, 3)
+    yb = torch.zeros(100, 140 * 3 + 7, dtype=torch.uint8, device="cuda")
+    dst = yb[:, :420].view(100, 140, 3)
+    rs.resize_batched([src], [(100, 140)], ["bicubic"], outs=[dst])
+    assert torch.equal(dst, rs.resize(src, (100, 140), "bicubic"))
+    assert (yb[:, 420:] == 0).all()
+    # overlapping destination and source is rejected
+    with pytest.raises(rs.ResampleError):
+        rs.resize_batched([src, src], [(100, 140), (20, 20)], ["bilinear", "bilinear"], outs=[dst, src[:20, :20]])
+
+
+def test_full_batch_workload(rs, oracle):
+    """256 RGB images, H and W uniform on 64..2048, scale uniform on [0.5, 4),
+    methods alternating bilinear / bicubic; sampled points of every image
+    against the oracle, every image against a per-image launch."""
+    from paper_1001_1718_gb300 import workloads
+    items = workloads.batch_spec(seed=4)
+    imgs = workloads.batch_images(items)
+    srcs = [torch.from_numpy(im).cuda() for im in imgs]
+    sizes = [(it.Ho, it.Wo) for it in items]
+    methods = [MN[it.method] for it in items]
+    outs = rs.resize_batched(srcs, sizes, methods)
+    torch.cuda.synchronize()
+    for k, (it, im, y) in enumerate(zip(items, imgs, outs)):
+        ys, xs = workloads.sample_points(k, it.Ho, it.Wo, 256)
+        ref = oracle.resize_points(im.astype(np.float64), it.Ho, it.Wo, it.method, 0, -0.5, ys, xs)
+        got = y[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()]
+        check(got, ref, "u8", it.method, 255.0, f"batch image {k}")
+        if k % 16 == 0:
+            assert torch.equal(y, rs.resize(srcs[k], sizes[k], methods[k]))
+    assert rs.debug_fault() == 0

@@ -1,0 +1,165 @@
+"""GPU forward parity: the CUDA path (through the C ABI) against the FP64
+oracle, element by element, on seeded inputs at sizes that span several
+tiles with ragged tails, plus degenerate shapes and guard-band checks."""
+import numpy as np
+import pytest
+import torch
+
+from _parity import check, to_storage, as_f64
+
+pytestmark = pytest.mark.gpu
+
+NN, BL, BC = 0, 1, 2
+MNAME = {NN: "nearest", BL: "bilinear", BC: "bicubic"}
+CNAME = {0: "asymmetric", 1: "half_pixel"}
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1718_gb300 as rs
+    return rs
+
+
+def _src(seed, shape, dtype):
+    r = np.random.default_rng(seed)
+    if dtype == "u8":
+        x = r.integers(0, 256, size=shape).astype(np.float64)
+    else:
+        x = r.standard_normal(shape) * 3.0
+    t = to_storage(x, dtype)
+    return t, as_f64(t)     # the oracle sees exactly the stored values
+
+
+SIZES = [
+    (37, 53, 91, 117),       # non-integer upscale, ragged
+    (300, 200, 600, 400),    # x2, several tiles
+    (257, 311, 128, 155),    # downscale
+    (64, 64, 64, 64),        # identity
+    (1, 50, 3, 77),          # one source row
+    (40, 1, 80, 5),          # one source column
+    (5, 7, 1, 1),            # single output pixel
+    (129, 517, 333, 1290),   # wide, many tiles
+]
+
+
+@pytest.mark.parametrize("method", [NN, BL, BC])
+@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
+@pytest.mark.parametrize("C", [1, 3, 4])
+def test_hwc_all_sizes(rs, oracle, method, coord, dtype, C):
+    for k, (H, W, Ho, Wo) in enumerate(SIZES):
+        t, x64 = _src(1000 + k, (H, W, C), dtype)
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], coord=CNAME[coord])
+        torch.cuda.synchronize()
+        ref = oracle.resize(x64, Ho, Wo, method, coord)
+        check(y, ref, dtype, method, np.abs(x64).max(), f"{MNAME[method]} {CNAME[coord]} {dtype} C={C} {H}x{W}->{Ho}x{Wo}")
+    assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("method", [NN, BL, BC])
+@pytest.mark.parametrize("impl", ["plain", "tiled"])
+def test_plain_and_tiled_nchw(rs, oracle, method, impl):
+    N, C, H, W = 2, 3, 75, 131
+    for (Ho, Wo), coord in (((150, 262), 0), ((37, 65), 1), ((201, 97), 0)):
+        t, x64 = _src(7, (N, C, H, W), "f32")
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl=impl)
+        torch.cuda.synchronize()
+        ref = oracle.resize_nchw(x64, Ho, Wo, method, coord)
+        check(y, ref, "f32", method, np.abs(x64).max(), f"nchw {impl} {MNAME[method]}")
+
+
+@pytest.mark.parametrize("tile", [(128, 4, 128), (256, 8, 256), (512, 32, 256), (1024, 64, 256), (128, 1, 128)])
+def test_explicit_tile_configs(rs, oracle, tile):
+    tw, th, nt = tile
+    t, x64 = _src(11, (203, 301, 3), "u8")
+    for method in (BL, BC):
+        for (Ho, Wo) in ((406, 602), (345, 511), (101, 150)):
+            try:
+                y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], tile=(tw, th), threads=nt)
+            except rs.ResampleError as e:
+                # A tall, wide tile at a downscale needs more shared memory
+                # than a block has: the call is refused before any launch.
+                assert e.status == 1 and Ho < 203 and tw * th >= 512 * 32
+                continue
+            torch.cuda.synchronize()
+            check(y, oracle.resize(x64, Ho, Wo, method), "u8", method, 255.0, f"tile {tile}")
+
+
+def test_plain_kernel_block_shapes(rs, oracle):
+    """The paper's tile-dimension sweep (Sec. III.B): every block shape gives
+    the same result."""
+    t, x64 = _src(12, (80, 80, 1), "u8")
+    ref = oracle.resize(x64, 160, 160, BL)
+    for bw, bh in ((32, 4), (8, 8), (4, 8), (8, 4), (32, 16), (16, 16), (64, 2), (1, 1)):
+        y = rs.resize(t.cuda(), (160, 160), "bilinear", impl="plain", tile=(bw, bh))
+        torch.cuda.synchronize()
+        check(y, ref, "u8", BL, 255.0, f"plain {bw}x{bh}")
+
+
+@pytest.mark.parametrize("method", [BL, BC])
+def test_x2_uint8_is_bit_exact(rs, oracle, method):
+    """Asymmetric x2: weights are dyadic (1/2; -1/16, 9/16), every FP32
+    product and sum of uint8 data is exact, so the GPU equals the FP64
+    oracle bit for bit."""
+    t, x64 = _src(13, (150, 173, 3), "u8")
+    y = rs.resize(t.cuda(), (300, 346), MNAME[method])
+    torch.cuda.synchronize()
+    q = oracle.quantize_u8(oracle.resize(x64, 300, 346, method))
+    assert np.array_equal(y.cpu().numpy(), q)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
+@pytest.mark.parametrize("method", [NN, BL, BC])
+def test_identity_is_exact(rs, method, dtype):
+    t, _ = _src(14, (33, 47, 3), dtype)
+    for coord in ("asymmetric", "half_pixel"):
+        y = rs.resize(t.cuda(), (33, 47), MNAME[method], coord=coord)
+        assert torch.equal(y.cpu(), t)
+
+
+def test_guard_bands_and_pitched_rows(rs, oracle):
+    """Writes stay inside the output: guard bands around dst and the gaps of
+    pitched rows keep their canary values."""
+    H, W, C, Ho, Wo = 45, 61, 3, 97, 130
+    t, x64 = _src(15, (H, W, C), "u8")
+    src_pitch, dst_pitch = W * C + 13, Wo * C + 29
+    sbuf = torch.zeros(H * src_pitch + 64, dtype=torch.uint8)
+    sbuf[:H * src_pitch].view(H, src_pitch)[:, :W * C] = t.reshape(H, W * C)
+    guard = 4096
+    dbuf = torch.full((guard + Ho * dst_pitch + guard,), 0xA5, dtype=torch.uint8, device="cuda")
+    s = sbuf.cuda()
+    src = s[:H * src_pitch].view(H, src_pitch)[:, :W * C].view(H, W, C)
+    dst = dbuf[guard:guard + Ho * dst_pitch].view(Ho, dst_pitch)[:, :Wo * C].view(Ho, Wo, C)
+    for method in (NN, BL, BC):
+        dbuf.fill_(0xA5)
+        rs.resize(src, (Ho, Wo), MNAME[method], out=dst)
+        torch.cuda.synchronize()
+        d = dbuf.cpu().numpy()
+        assert (d[:guard] == 0xA5).all() and (d[guard + Ho * dst_pitch:] == 0xA5).all()
+        rows = d[guard:guard + Ho * dst_pitch].reshape(Ho, dst_pitch)
+        assert (rows[:, Wo * C:] == 0xA5).all()
+        check(dst, oracle.resize(x64, Ho, Wo, method), "u8", method, 255.0, "pitched")
+
+
+def test_invalid_call_writes_nothing(rs):
+    """A call that fails validation launches nothing: dst keeps its contents."""
+    x = torch.zeros(64, 64, 3, dtype=torch.uint8, device="cuda")
+    y = torch.full((128, 128, 3), 7, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rs.ResampleError):
+        rs.resize(x, (128, 128), "bicubic", coord=5)
+    with pytest.raises(rs.ResampleError):
+        rs.resize(x, (128, 128), "bicubic", out=y, tile=(100, 8))   # tile width not a multiple of 4
+    torch.cuda.synchronize()
+    assert (y == 7).all()
+
+
+def test_half_pixel_bicubic_matches_torch(rs):
+    """Secondary cross-check: torch's bicubic (align_corners=False) is the
+    half-pixel map with a = -3/4."""
+    x = torch.randn(2, 3, 50, 70, device="cuda")
+    for size in ((100, 140), (33, 41), (77, 200)):
+        y = rs.resize(x, size, "bicubic", layout="nchw", coord="half_pixel", cubic_a=-0.75)
+        r = torch.nn.functional.interpolate(x, size=size, mode="bicubic", align_corners=False)
+        assert (y - r).abs().max().item() < 1e-4
