@@ -60,11 +60,21 @@ typedef enum { RS_U8 = 0, RS_F16 = 1, RS_BF16 = 2, RS_F32 = 3 } rs_dtype;
 typedef enum { RS_NEAREST = 0, RS_BILINEAR = 1, RS_BICUBIC = 2 } rs_method;
 typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
 
-/* Kernel selection. AUTO = the tiled kernel with the tuned (or default)
- * configuration. PLAIN = one thread per output pixel reading its taps from
- * global memory, thread blocks of tile_w x tile_h threads (default 32 x 4):
- * the paper's kernel (Sec. III.A, Eq. 6), kept as the comparison baseline. */
-typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2 } rs_impl;
+/* Kernel selection.
+ * AUTO   = the tuned (or default) kernel for the problem: the streaming
+ *          kernel when its footprint fits in shared memory, else TILED.
+ * STREAM = one block per (column strip, band of rows), walking down the band
+ *          in chunks; every source row is staged and horizontally
+ *          interpolated once per strip; loads of the next chunk are issued
+ *          while the current one computes. tile_w = strip width in output
+ *          elements, tile_h = rows per chunk, waves = blocks per resident
+ *          block slot (sets the band height).
+ * TILED  = one block per output tile of tile_w elements x tile_h rows with
+ *          `threads` threads; the footprint and halo are staged per tile.
+ * PLAIN  = one thread per output pixel reading its taps from global memory,
+ *          thread blocks of tile_w x tile_h threads (default 32 x 4): the
+ *          paper's kernel (Sec. III.A, Eq. 6), kept as the comparison row. */
+typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_STREAM = 3 } rs_impl;
 
 typedef struct {
     int32_t coord;      /* rs_coord; default RS_COORD_ASYMMETRIC */
@@ -74,7 +84,8 @@ typedef struct {
                            TILED: output elements per tile row (multiple of 4*32). */
     int32_t tile_h;     /* 0 = default. PLAIN: threads along y. TILED: output rows per tile. */
     int32_t threads;    /* 0 = default. TILED: threads per block (128 or 256). */
-    int32_t reserved[2];
+    int32_t waves;      /* 0 = default. STREAM: blocks per resident block slot. */
+    int32_t reserved;
 } rs_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -183,8 +194,9 @@ rs_status rs_batched_plan_launch(rs_batched_plan* plan, void* stream);
 rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
 
 /*
- * Autotuner. A tile configuration of the tiled kernel: tile_w output
- * elements x tile_h output rows per thread block of `threads` threads.
+ * Autotuner. A configuration is a kernel (STREAM or TILED) and its shape:
+ * STREAM strip width tile_w x chunk height tile_h with `waves` blocks per
+ * resident slot; TILED tile_w elements x tile_h rows with `threads` threads.
  * rs_autotune times every candidate configuration on the caller's buffers
  * (dst is overwritten; the stream is synchronised while it runs) and stores
  * the fastest in the in-process cache, keyed by GPU, dtype, method, channel
@@ -192,7 +204,8 @@ rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
  * The cache can be saved to and loaded from a text file.
  */
 typedef struct {
-    int32_t tile_w, tile_h, threads;
+    int32_t impl;       /* RS_IMPL_STREAM or RS_IMPL_TILED */
+    int32_t tile_w, tile_h, threads, waves;
     float best_us;      /* measured time of the chosen configuration */
     float default_us;   /* measured time of the default configuration */
     int32_t candidates; /* number of configurations timed */

@@ -22,7 +22,9 @@ from ._binding import ResampleError, lib
 
 METHODS = {"nearest": B.RS_NEAREST, "bilinear": B.RS_BILINEAR, "bicubic": B.RS_BICUBIC}
 COORDS = {"asymmetric": B.RS_COORD_ASYMMETRIC, "half_pixel": B.RS_COORD_HALF_PIXEL}
-IMPLS = {"auto": B.RS_IMPL_AUTO, "tiled": B.RS_IMPL_TILED, "plain": B.RS_IMPL_PLAIN}
+IMPLS = {"auto": B.RS_IMPL_AUTO, "tiled": B.RS_IMPL_TILED, "plain": B.RS_IMPL_PLAIN,
+         "stream": B.RS_IMPL_STREAM}
+IMPL_NAMES = {v: k for k, v in IMPLS.items()}
 DTYPES = {torch.uint8: B.RS_U8, torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16,
           torch.float32: B.RS_F32}
 
@@ -105,16 +107,19 @@ def _stream(t: torch.Tensor) -> int:
     return torch.cuda.current_stream(t.device).cuda_stream
 
 
-def _opts(coord, cubic_a, impl, tile, threads) -> B.RsOptions:
+def _opts(coord, cubic_a, impl, tile, threads, waves=0) -> B.RsOptions:
     tw, th = (tile or (0, 0))
     return B.options(_code(COORDS, coord, "coord"), float(cubic_a), _code(IMPLS, impl, "impl"),
-                     int(tw), int(th), int(threads))
+                     int(tw), int(th), int(threads), int(waves))
 
 
 def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: str = "hwc",
            coord="asymmetric", cubic_a: float = -0.5, impl="auto", tile=None, threads: int = 0,
-           out: torch.Tensor | None = None) -> torch.Tensor:
-    """Resample x to size (Ho, Wo). Same dtype out; FP32 arithmetic."""
+           waves: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Resample x to size (Ho, Wo). Same dtype out; FP32 arithmetic.
+
+    impl: "auto" (tuned or default kernel), "stream", "tiled" or "plain";
+    tile = (tile_w, tile_h) and threads / waves override the kernel shape."""
     _require_cuda(x)
     Ho, Wo = int(size[0]), int(size[1])
     if out is None:
@@ -123,7 +128,7 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
     if out.dtype != x.dtype:
         raise ValueError("out must have the dtype of x")
     Li, Lo = _layout(x, layout), _layout(out, layout)
-    o = _opts(coord, cubic_a, impl, tile, threads)
+    o = _opts(coord, cubic_a, impl, tile, threads, waves)
     with torch.cuda.device(x.device):
         B.check(lib().rs_resize_ex(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo),
                                    _dtype(x), _code(METHODS, method, "method"), ctypes.byref(o),
@@ -282,8 +287,9 @@ def autotune(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric",
         B.check(lib().rs_autotune(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo), _dtype(x),
                                   _code(METHODS, method, "method"), ctypes.byref(o), _stream(x),
                                   ctypes.byref(best)), "rs_autotune")
-    return {"tile_w": best.tile_w, "tile_h": best.tile_h, "threads": best.threads,
-            "best_us": best.best_us, "default_us": best.default_us, "candidates": best.candidates}
+    return {"impl": IMPL_NAMES.get(best.impl, best.impl), "tile_w": best.tile_w, "tile_h": best.tile_h,
+            "threads": best.threads, "waves": best.waves, "best_us": best.best_us,
+            "default_us": best.default_us, "candidates": best.candidates}
 
 
 def tile_config(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric", cubic_a=-0.5) -> dict:
@@ -295,7 +301,8 @@ def tile_config(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetri
     B.check(lib().rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), _dtype(x),
                                      _code(METHODS, method, "method"), ctypes.byref(o), ctypes.byref(c)),
             "rs_tile_config_for")
-    return {"tile_w": c.tile_w, "tile_h": c.tile_h, "threads": c.threads}
+    return {"impl": IMPL_NAMES.get(c.impl, c.impl), "tile_w": c.tile_w, "tile_h": c.tile_h,
+            "threads": c.threads, "waves": c.waves}
 
 
 def tune_cache_save(path: str) -> None:

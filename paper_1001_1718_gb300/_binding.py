@@ -15,13 +15,13 @@ RS_OK, RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED, RS_ERR_ALIGNMENT, RS_ERR_WORKSPAC
 RS_U8, RS_F16, RS_BF16, RS_F32 = range(4)
 RS_NEAREST, RS_BILINEAR, RS_BICUBIC = range(3)
 RS_COORD_ASYMMETRIC, RS_COORD_HALF_PIXEL = range(2)
-RS_IMPL_AUTO, RS_IMPL_TILED, RS_IMPL_PLAIN = range(3)
+RS_IMPL_AUTO, RS_IMPL_TILED, RS_IMPL_PLAIN, RS_IMPL_STREAM = range(4)
 
 
 class RsOptions(ctypes.Structure):
     _fields_ = [("coord", ctypes.c_int32), ("cubic_a", ctypes.c_float), ("impl", ctypes.c_int32),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("waves", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RsLayout(ctypes.Structure):
@@ -38,7 +38,8 @@ class RsImageDesc(ctypes.Structure):
 
 
 class RsTileConfig(ctypes.Structure):
-    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("threads", ctypes.c_int32),
+    _fields_ = [("impl", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("best_us", ctypes.c_float), ("default_us", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
@@ -112,9 +113,9 @@ def check(status: int, where: str) -> None:
 
 
 def options(coord: int = RS_COORD_ASYMMETRIC, cubic_a: float = -0.5, impl: int = RS_IMPL_AUTO,
-            tile_w: int = 0, tile_h: int = 0, threads: int = 0) -> RsOptions:
+            tile_w: int = 0, tile_h: int = 0, threads: int = 0, waves: int = 0) -> RsOptions:
     o = RsOptions()
     lib().rs_options_init(ctypes.byref(o))
     o.coord, o.cubic_a, o.impl = coord, cubic_a, impl
-    o.tile_w, o.tile_h, o.threads = tile_w, tile_h, threads
+    o.tile_w, o.tile_h, o.threads, o.waves = tile_w, tile_h, threads, waves
     return o

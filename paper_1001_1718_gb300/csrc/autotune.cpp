@@ -1,10 +1,10 @@
-// Autotuner of the tiled forward kernel and its cache.
+// Kernel choice, autotuner and tuning cache of the forward path.
 //
 // The paper's question (Sec. IV, V) is whether one tile shape suits every
 // GPU and every scale; its answer is that it does not always. Here every
 // problem class (GPU, dtype, method, channel layout, coordinate mode, scale
-// class per axis, output size class) gets its own tile shape, chosen by
-// timing the candidates on the caller's buffers with CUDA events.
+// class per axis, output size class) gets its own kernel and shape, chosen
+// by timing the candidates on the caller's buffers with CUDA events.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -20,7 +20,7 @@
 namespace rs {
 
 struct Tuned {
-    int tile_w, tile_h, threads;
+    int impl, tile_w, tile_h, threads, waves;
 };
 
 static std::mutex g_tune_mu;
@@ -42,6 +42,13 @@ static std::string tune_key(const Geom& g, int method, int dtype)
     return buf;
 }
 
+static bool valid_tuned(const Tuned& t)
+{
+    if (t.impl == RS_IMPL_STREAM) return t.tile_w > 0 && t.tile_h > 0 && t.waves > 0;
+    if (t.impl == RS_IMPL_TILED) return t.tile_w > 0 && t.tile_h > 0 && (t.threads == 128 || t.threads == 256);
+    return false;
+}
+
 static bool load_file(const char* path)
 {
     FILE* f = std::fopen(path, "r");
@@ -50,12 +57,12 @@ static bool load_file(const char* path)
     std::map<std::string, Tuned> add;
     bool versioned = false;
     while (std::fgets(line, sizeof line, f)) {
-        if (std::strncmp(line, "# resample-tune v1", 18) == 0) { versioned = true; continue; }
+        if (std::strncmp(line, "# resample-tune v2", 18) == 0) { versioned = true; continue; }
         if (line[0] == '#' || line[0] == '\n') continue;
         char key[256];
         Tuned t;
-        if (std::sscanf(line, "%255s %d %d %d", key, &t.tile_w, &t.tile_h, &t.threads) == 4 &&
-            t.tile_w > 0 && t.tile_h > 0 && (t.threads == 128 || t.threads == 256))
+        if (std::sscanf(line, "%255s %d %d %d %d %d", key, &t.impl, &t.tile_w, &t.tile_h, &t.threads, &t.waves) == 6 &&
+            valid_tuned(t))
             add[key] = t;
     }
     std::fclose(f);
@@ -72,49 +79,90 @@ static void load_env_once()
     if (p && *p) load_file(p);
 }
 
-rs_status choose_tile(const Geom& g, int method, int dtype, const rs_options& o, TileCfg& cfg)
+static bool make_choice(const Geom& g, int method, int dtype, const void* src, const Tuned& t, KernelChoice& k)
 {
-    if (o.tile_w || o.tile_h || o.threads) {
-        TileCfg d = tiled_default(g, method);
-        cfg = TileCfg{o.tile_w ? o.tile_w : d.tile_w, o.tile_h ? o.tile_h : d.tile_h,
-                      o.threads ? o.threads : d.threads, 0, 0, 0};
-        return tiled_config(g, method, cfg) ? RS_OK : RS_ERR_INVALID_ARG;
+    k.impl = t.impl;
+    if (t.impl == RS_IMPL_STREAM) {
+        k.stream = StreamCfg{};
+        k.stream.tile_w = t.tile_w;
+        k.stream.chunk_h = t.tile_h;
+        k.stream.waves = t.waves;
+        return stream_config(g, method, dtype, src, k.stream);
     }
-    if (o.impl == RS_IMPL_AUTO) {
+    k.tile = TileCfg{t.tile_w, t.tile_h, t.threads, 0, 0, 0};
+    return tiled_config(g, method, k.tile);
+}
+
+static bool default_choice(const Geom& g, int method, int dtype, const void* src, KernelChoice& k)
+{
+    StreamCfg sc = stream_default(g, method, dtype, src);
+    if (sc.tile_w) {
+        sc.waves = 4;
+        k.impl = RS_IMPL_STREAM;
+        k.stream = sc;
+        return true;
+    }
+    k.impl = RS_IMPL_TILED;
+    k.tile = tiled_default(g, method);
+    return k.tile.tile_w != 0;
+}
+
+rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, const rs_options& o,
+                        KernelChoice& k)
+{
+    const bool explicit_shape = o.tile_w || o.tile_h || o.threads || o.waves;
+    if (o.impl == RS_IMPL_STREAM || (o.impl == RS_IMPL_AUTO && explicit_shape && !o.threads)) {
+        StreamCfg d = stream_default(g, method, dtype, src);
+        Tuned t{RS_IMPL_STREAM, o.tile_w ? o.tile_w : (d.tile_w ? d.tile_w : 512),
+                o.tile_h ? o.tile_h : (d.chunk_h ? d.chunk_h : 8), 256, o.waves ? o.waves : 4};
+        return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
+    }
+    if (o.impl == RS_IMPL_TILED || (o.impl == RS_IMPL_AUTO && o.threads)) {
+        if (explicit_shape) {
+            TileCfg d = tiled_default(g, method);
+            Tuned t{RS_IMPL_TILED, o.tile_w ? o.tile_w : d.tile_w, o.tile_h ? o.tile_h : d.tile_h,
+                    o.threads ? o.threads : d.threads, 0};
+            return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
+        }
+        k.impl = RS_IMPL_TILED;
+        k.tile = tiled_default(g, method);
+        return k.tile.tile_w ? RS_OK : RS_ERR_UNSUPPORTED;
+    }
+    {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         load_env_once();
         auto it = g_tune.find(tune_key(g, method, dtype));
-        if (it != g_tune.end()) {
-            cfg = TileCfg{it->second.tile_w, it->second.tile_h, it->second.threads, 0, 0, 0};
-            if (tiled_config(g, method, cfg)) return RS_OK;
-        }
+        if (it != g_tune.end() && make_choice(g, method, dtype, src, it->second, k)) return RS_OK;
     }
-    cfg = tiled_default(g, method);
-    return cfg.tile_w ? RS_OK : RS_ERR_UNSUPPORTED;
+    return default_choice(g, method, dtype, src, k) ? RS_OK : RS_ERR_UNSUPPORTED;
 }
 
-// Median time in microseconds of `reps` launches, measured as 3 batches.
-static cudaError_t time_cfg(const Geom& g, int method, int dtype, const void* src, void* dst,
-                            const TileCfg& cfg, cudaStream_t st, float* us)
+cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src, void* dst, const KernelChoice& k,
+                          cudaStream_t st)
+{
+    if (k.impl == RS_IMPL_STREAM) return launch_stream(g, method, dtype, src, dst, k.stream, st);
+    return launch_tiled(g, method, dtype, src, dst, k.tile, st);
+}
+
+// Median time in microseconds of one launch, from 3 batches sized to ~2 ms.
+static cudaError_t time_choice(const Geom& g, int method, int dtype, const void* src, void* dst,
+                               const KernelChoice& k, cudaStream_t st, float* us)
 {
     cudaEvent_t a, b;
     cudaError_t e = cudaEventCreate(&a);
     if (e != cudaSuccess) return e;
     if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
-    float samples[3];
+    float samples[3] = {0, 0, 0};
     int reps = 1;
-    for (int k = -1; k < 3 && e == cudaSuccess; ++k) {
+    for (int it = -1; it < 3 && e == cudaSuccess; ++it) {
         cudaEventRecord(a, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_tiled(g, method, dtype, src, dst, cfg, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_choice(g, method, dtype, src, dst, k, st);
         cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (k < 0) {   // warm-up launch sizes the batches to ~2 ms each
-            reps = std::max(1, std::min(50, (int)std::ceil(2.0f / std::max(ms, 1e-3f))));
-        } else {
-            samples[k] = 1000.0f * ms / reps;
-        }
+        if (it < 0) reps = std::max(1, std::min(50, (int)std::ceil(2.0f / std::max(ms, 1e-3f))));
+        else samples[it] = 1000.0f * ms / reps;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -124,52 +172,65 @@ static cudaError_t time_cfg(const Geom& g, int method, int dtype, const void* sr
     return cudaSuccess;
 }
 
+static Tuned to_tuned(const KernelChoice& k)
+{
+    if (k.impl == RS_IMPL_STREAM) return Tuned{RS_IMPL_STREAM, k.stream.tile_w, k.stream.chunk_h, 256, k.stream.waves};
+    return Tuned{RS_IMPL_TILED, k.tile.tile_w, k.tile.tile_h, k.tile.threads, 0};
+}
+
+static void fill(rs_tile_config* c, const Tuned& t)
+{
+    c->impl = t.impl;
+    c->tile_w = t.tile_w;
+    c->tile_h = t.tile_h;
+    c->threads = t.threads;
+    c->waves = t.waves;
+}
+
 }  // namespace rs
 
 using namespace rs;
 
 extern "C" {
 
-rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_layout* out,
-                      rs_dtype dtype, rs_method method, const rs_options* opt, void* stream,
-                      rs_tile_config* best)
+rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_layout* out, rs_dtype dtype,
+                      rs_method method, const rs_options* opt, void* stream, rs_tile_config* best)
 {
     rs_options o = options_or_default(opt);
     Geom g;
     rs_status s = make_geom(src, in, dst, out, dtype, method, o, g);
     if (s != RS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    static const int widths[] = {128, 256, 512, 1024};
-    static const int heights[] = {4, 8, 16, 32, 64};
-    static const int threads[] = {128, 256};
-    TileCfg def = tiled_default(g, method);
-    if (!def.tile_w) return RS_ERR_UNSUPPORTED;
+    std::vector<Tuned> cands;
+    for (int tw : {128, 256, 512, 1024})
+        for (int ch : {4, 8, 16, 32})
+            for (int wv : {2, 4, 8}) cands.push_back(Tuned{RS_IMPL_STREAM, tw, ch, 256, wv});
+    for (int tw : {128, 256, 512, 1024})
+        for (int th : {4, 8, 16, 32, 64})
+            for (int nt : {128, 256}) cands.push_back(Tuned{RS_IMPL_TILED, tw, th, nt, 0});
+    KernelChoice def;
+    if (!default_choice(g, method, dtype, src, def)) return RS_ERR_UNSUPPORTED;
     float def_us = 0.0f;
-    cudaError_t e = time_cfg(g, method, dtype, src, dst, def, st, &def_us);
+    cudaError_t e = time_choice(g, method, dtype, src, dst, def, st, &def_us);
     if (e != cudaSuccess) return cuda_status(e);
-    TileCfg bestc = def;
+    Tuned bestt = to_tuned(def);
     float best_us = def_us;
     int n = 1;
-    for (int tw : widths)
-        for (int th : heights)
-            for (int nt : threads) {
-                TileCfg c{tw, th, nt, 0, 0, 0};
-                if (!tiled_config(g, method, c)) continue;
-                if (c.tile_w == def.tile_w && c.tile_h == def.tile_h && c.threads == def.threads) continue;
-                float us = 0.0f;
-                e = time_cfg(g, method, dtype, src, dst, c, st, &us);
-                if (e != cudaSuccess) return cuda_status(e);
-                ++n;
-                if (us < best_us) { best_us = us; bestc = c; }
-            }
+    for (const Tuned& t : cands) {
+        KernelChoice k;
+        if (!make_choice(g, method, dtype, src, t, k)) continue;
+        float us = 0.0f;
+        e = time_choice(g, method, dtype, src, dst, k, st, &us);
+        if (e != cudaSuccess) return cuda_status(e);
+        ++n;
+        if (us < best_us) { best_us = us; bestt = t; }
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[tune_key(g, method, dtype)] = Tuned{bestc.tile_w, bestc.tile_h, bestc.threads};
+        g_tune[tune_key(g, method, dtype)] = bestt;
     }
     if (best) {
-        best->tile_w = bestc.tile_w;
-        best->tile_h = bestc.tile_h;
-        best->threads = bestc.threads;
+        fill(best, bestt);
         best->best_us = best_us;
         best->default_us = def_us;
         best->candidates = n;
@@ -186,11 +247,11 @@ rs_status rs_tile_config_for(const rs_layout* in, const rs_layout* out, rs_dtype
     LayoutInfo li, lo;
     rs_status s = geom_from_layouts(in, out, dtype, method, o, g, li, lo);
     if (s != RS_OK) return s;
-    TileCfg c;
-    if ((s = choose_tile(g, method, dtype, o, c)) != RS_OK) return s;
-    cfg->tile_w = c.tile_w;
-    cfg->tile_h = c.tile_h;
-    cfg->threads = c.threads;
+    // Assume 256-byte aligned buffers (as cudaMalloc returns).
+    static const char* const aligned = reinterpret_cast<const char*>(256);
+    KernelChoice k;
+    if ((s = choose_kernel(g, method, dtype, aligned, o, k)) != RS_OK) return s;
+    fill(cfg, to_tuned(k));
     cfg->best_us = 0.0f;
     cfg->default_us = 0.0f;
     cfg->candidates = 0;
@@ -203,9 +264,10 @@ rs_status rs_tune_cache_save(const char* path)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     FILE* f = std::fopen(path, "w");
     if (!f) return RS_ERR_INVALID_ARG;
-    std::fprintf(f, "# resample-tune v1\n");
+    std::fprintf(f, "# resample-tune v2: key impl tile_w tile_h threads waves\n");
     for (auto& kv : g_tune)
-        std::fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.tile_w, kv.second.tile_h, kv.second.threads);
+        std::fprintf(f, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.impl, kv.second.tile_w,
+                     kv.second.tile_h, kv.second.threads, kv.second.waves);
     std::fclose(f);
     return RS_OK;
 }

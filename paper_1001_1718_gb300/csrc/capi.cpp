@@ -30,8 +30,8 @@ rs_status check_options(const rs_options& o, int method)
 {
     if (o.coord != RS_COORD_ASYMMETRIC && o.coord != RS_COORD_HALF_PIXEL) return RS_ERR_INVALID_ARG;
     if (!std::isfinite(o.cubic_a)) return RS_ERR_INVALID_ARG;
-    if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_PLAIN) return RS_ERR_INVALID_ARG;
-    if (o.tile_w < 0 || o.tile_h < 0 || o.threads < 0) return RS_ERR_INVALID_ARG;
+    if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_STREAM) return RS_ERR_INVALID_ARG;
+    if (o.tile_w < 0 || o.tile_h < 0 || o.threads < 0 || o.waves < 0) return RS_ERR_INVALID_ARG;
     if (method < RS_NEAREST || method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
     return RS_OK;
 }
@@ -177,10 +177,9 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst, const rs
         if (bw * bh > 1024 || bw < 1 || bh < 1 || bh > 64) return RS_ERR_INVALID_ARG;
         return cuda_status(launch_plain(g, method, dtype, src, dst, bw, bh, st));
     }
-    TileCfg cfg;
-    s = choose_tile(g, method, dtype, o, cfg);
-    if (s != RS_OK) return s;
-    return cuda_status(launch_tiled(g, method, dtype, src, dst, cfg, st));
+    KernelChoice k;
+    if ((s = choose_kernel(g, method, dtype, src, o, k)) != RS_OK) return s;
+    return cuda_status(launch_choice(g, method, dtype, src, dst, k, st));
 }
 
 rs_status rs_resize(const void* src, int H, int W, int C, rs_dtype dtype, void* dst, int Ho, int Wo,

@@ -22,9 +22,17 @@ rs_status geom_from_layouts(const rs_layout* in, const rs_layout* out, int dtype
 rs_status make_geom(const void* src, const rs_layout* in, const void* dst, const rs_layout* out,
                     int dtype, int method, const rs_options& o, Geom& g);
 
-// Tile configuration for a forward call: explicit options, else the tuning
-// cache, else the default.
-rs_status choose_tile(const Geom& g, int method, int dtype, const rs_options& o, TileCfg& cfg);
+// Kernel and configuration for a forward call: explicit options, else the
+// tuning cache, else the default (streaming kernel when it fits).
+struct KernelChoice {
+    int impl;        // RS_IMPL_STREAM or RS_IMPL_TILED
+    TileCfg tile;
+    StreamCfg stream;
+};
+rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, const rs_options& o,
+                        KernelChoice& k);
+cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src, void* dst,
+                          const KernelChoice& k, cudaStream_t st);
 
 cudaError_t read_fault(cudaStream_t st, unsigned int* code);
 

@@ -55,6 +55,18 @@ struct TileCfg {
     size_t smem;
 };
 
+// Configuration of the streaming forward kernel: strips of tile_w output
+// elements, chunks of chunk_h output rows, bands of band_h rows per block
+// (0 = chosen from occupancy and `waves` blocks per resident slot), an
+// rh-row ring (power of two) of horizontally interpolated rows, rs_rows
+// staged source rows of swe_max elements; vec = 16-byte loads.
+struct StreamCfg {
+    int tile_w, chunk_h, band_h, waves;
+    int rh, rs_rows, swe_max, vec;
+    int band_cap;   // rows of the per-block row-tap table (band_h <= band_cap)
+    size_t smem;
+};
+
 int method_taps(int method);
 size_t dtype_size(int dtype);
 
@@ -73,6 +85,10 @@ TileCfg tiled_default(const Geom& g, int method);
 
 cudaError_t launch_tiled(const Geom& g, int method, int dtype, const void* src, void* dst,
                          const TileCfg& cfg, cudaStream_t st);
+bool stream_config(const Geom& g, int method, int dtype, const void* src, StreamCfg& c);
+StreamCfg stream_default(const Geom& g, int method, int dtype, const void* src);
+cudaError_t launch_stream(const Geom& g, int method, int dtype, const void* src, void* dst, StreamCfg c,
+                          cudaStream_t st);
 cudaError_t launch_plain(const Geom& g, int method, int dtype, const void* src, void* dst,
                          int bw, int bh, cudaStream_t st);
 

@@ -46,7 +46,7 @@ def test_status_strings_and_defaults(L):
     assert L.rs_status_string(0) == b"ok"
     assert L.rs_status_string(4).startswith(b"workspace")
     o = B.options()
-    assert (o.coord, o.cubic_a, o.impl, o.tile_w, o.tile_h, o.threads) == (0, -0.5, 0, 0, 0, 0)
+    assert (o.coord, o.cubic_a, o.impl, o.tile_w, o.tile_h, o.threads, o.waves) == (0, -0.5, 0, 0, 0, 0, 0)
     lay = L.rs_layout_hwc(2, 5, 7, 3)
     assert (lay.N, lay.C, lay.H, lay.W, lay.px_stride, lay.c_stride, lay.row_pitch, lay.n_stride) == \
         (2, 3, 5, 7, 3, 1, 21, 105)
@@ -108,17 +108,34 @@ def test_layout_validation(L):
 
 def test_tune_cache_file_roundtrip(L, tmp_path):
     p = tmp_path / "tune.txt"
-    p.write_text("# resample-tune v1\nsms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27 512 16 256\nbogus line\n")
+    key = "sms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27"
+    p.write_text(f"# resample-tune v2\n{key} 3 512 16 256 4\nbogus line\nk2 1 512 16 100 0\n")
     assert L.rs_tune_cache_load(str(p).encode()) == 0
     q = tmp_path / "out.txt"
     assert L.rs_tune_cache_save(str(q).encode()) == 0
-    assert "sms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27 512 16 256" in q.read_text()
+    text = q.read_text()
+    assert f"{key} 3 512 16 256 4" in text
+    assert "k2" not in text            # invalid thread count: dropped
     stale = tmp_path / "stale.txt"
-    stale.write_text("key 1 2 3\n")   # no version header: ignored
+    stale.write_text("# resample-tune v1\nkey 512 16 256\n")   # old format: ignored
     assert L.rs_tune_cache_load(str(stale).encode()) != 0
     L.rs_tune_cache_clear()
     assert L.rs_tune_cache_save(str(q).encode()) == 0
-    assert q.read_text().strip() == "# resample-tune v1"
+    assert q.read_text().strip().startswith("# resample-tune v2")
+    assert len(q.read_text().strip().splitlines()) == 1
+
+
+def test_tile_config_query_without_buffers(L):
+    """The kernel AUTO would pick for a problem, from layouts alone."""
+    import paper_1001_1718_gb300 as rs
+    from paper_1001_1718_gb300 import _binding as B
+    Li, Lo = L.rs_layout_hwc(1, 4096, 4096, 3), L.rs_layout_hwc(1, 8192, 8192, 3)
+    c = B.RsTileConfig()
+    # num_sms() falls back to 1 without a GPU; the choice itself is host logic
+    assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_U8, B.RS_BICUBIC, None,
+                                ctypes.byref(c)) == 0
+    assert c.impl == B.RS_IMPL_STREAM and c.tile_w > 0 and c.tile_h > 0
+    del rs
 
 
 def test_product_path_refuses_cpu_tensors():
