@@ -180,6 +180,35 @@ rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype,
                             const rs_options* opt, void* stream);
 
 /*
+ * Ragged batch without any allocation, for callers that cannot obtain
+ * device memory for a workspace: code under an allocator that owns all
+ * device memory (a framework's caching pool, a fixed memory budget),
+ * serving paths that forbid allocation after start-up because cudaMalloc
+ * can block or fail, and plugin hosts that only hand out input and output
+ * buffers. The paper has no counterpart; this is a deployment variant of
+ * rs_resize_batched with the same arguments minus the workspace, and the
+ * same results.
+ *
+ * The work list goes into a fixed array of device memory declared inside
+ * the library (static __device__, RS_NOALLOC_MAX_IMAGES descriptors, about
+ * 352 KB); every GPU that loads the library holds it until the process
+ * exits. Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ *   - n > RS_NOALLOC_MAX_IMAGES returns RS_ERR_WORKSPACE, before any work.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array and overwrites it (nothing in it needs
+ *     to start at zero: each call writes all it reads). Calls whose work
+ *     overlaps on the GPU (for example on two streams at once) race on it;
+ *     calls on one stream run in order and are safe.
+ *   - The descriptors are copied from host memory on `stream` before the
+ *     launch; src / dst stay owned by the caller as in rs_resize_batched.
+ */
+#define RS_NOALLOC_MAX_IMAGES 4096
+rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs_dtype dtype,
+                                    const rs_options* opt, void* stream);
+
+/*
  * Replayable batch: the work list is uploaded once and the persistent launch
  * is recorded as a CUDA graph; each rs_batched_plan_launch replays it on a
  * stream. The plan refers to the descriptors' src / dst buffers and to

@@ -16,6 +16,7 @@ RS_U8, RS_F16, RS_BF16, RS_F32 = range(4)
 RS_NEAREST, RS_BILINEAR, RS_BICUBIC = range(3)
 RS_COORD_ASYMMETRIC, RS_COORD_HALF_PIXEL = range(2)
 RS_IMPL_AUTO, RS_IMPL_TILED, RS_IMPL_PLAIN, RS_IMPL_STREAM = range(4)
+RS_NOALLOC_MAX_IMAGES = 4096
 
 
 class RsOptions(ctypes.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
                                  ctypes.POINTER(RsOptions), P, SZ, P]),
     "rs_resize_batched_workspace": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, ctypes.POINTER(SZ)]),
     "rs_resize_batched": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, P, SZ, ctypes.POINTER(RsOptions), P]),
+    "rs_resize_batched_noalloc": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, ctypes.POINTER(RsOptions), P]),
     "rs_batched_plan_create": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, P, SZ, ctypes.POINTER(RsOptions),
                                      P, ctypes.POINTER(P)]),
     "rs_batched_plan_launch": (I32, [P, P]),

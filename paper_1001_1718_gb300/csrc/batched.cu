@@ -255,7 +255,136 @@ static rs_status check_ws(const BatchPlanHost& P, void* ws, size_t bytes)
     return RS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched resampling without any allocation.
+//
+// Some callers cannot obtain device memory for the workspace: code running
+// under an allocator that owns all device memory (a framework's caching
+// pool or a fixed memory budget), real-time serving paths that forbid any
+// allocation after start-up because cudaMalloc can block or fail, and plugin
+// hosts that only hand out their own input and output buffers. For them the
+// work list lives in a fixed array of device memory that the library itself
+// declares (file scope, `static __device__`), so no call allocates: every GPU
+// that loads the library holds kNoAllocBytes of it until the process exits.
+//
+// In host code the array's name is only a host-side handle, not a device
+// address; its device address is looked up per device with
+// cudaGetSymbolAddress (on the first call made on that device, with that
+// device current) and passed to the kernel like any other pointer.
+static constexpr int kNoAllocMaxImages = 4096;
+static constexpr size_t kNoAllocImgBytes = ((sizeof(BatchImage) * kNoAllocMaxImages + 255) / 256) * 256;
+static constexpr size_t kNoAllocBytes = kNoAllocImgBytes + sizeof(int64_t) * (kNoAllocMaxImages + 1);
+static __device__ __align__(256) unsigned char g_batch_scratch[kNoAllocBytes];
+
+static constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;                               // guards everything below
+static void* g_noalloc_dev[kNoAllocMaxDevices];               // device address per device
+static BatchImage g_noalloc_imgs[kNoAllocMaxImages];           // host staging (no heap use)
+static int64_t g_noalloc_start[kNoAllocMaxImages + 1];
+
+// Same validation and tiling as batch_prepare, written into the fixed
+// host staging arrays instead of vectors.
+static rs_status noalloc_prepare(const rs_image_desc* d, int n, int dtype, const rs_options& o, size_t& smem,
+                                 int& threads)
+{
+    if (!d || n < 1) return RS_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxImages) return RS_ERR_WORKSPACE;
+    if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
+    rs_status s = check_options(o, RS_BILINEAR);
+    if (s != RS_OK) return s;
+    const int tile_w = o.tile_w ? o.tile_w : 512;
+    const int h_cap = o.tile_h ? o.tile_h : 32;
+    threads = o.threads ? o.threads : 256;
+    if (threads != 128 && threads != 256) return RS_ERR_INVALID_ARG;
+    const int64_t es = (int64_t)dtype_size(dtype);
+    auto src_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.H - 1) * x.src_pitch + (int64_t)x.W * x.C) * es; };
+    auto dst_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.Ho - 1) * x.dst_pitch + (int64_t)x.Wo * x.C) * es; };
+    g_noalloc_start[0] = 0;
+    smem = 0;
+    for (int k = 0; k < n; ++k) {
+        const rs_image_desc& x = d[k];
+        if (!x.src || !x.dst) return RS_ERR_INVALID_ARG;
+        if (!dim_ok(x.H) || !dim_ok(x.W) || !dim_ok(x.Ho) || !dim_ok(x.Wo)) return RS_ERR_INVALID_ARG;
+        if (x.C < 1 || x.C > 4) return RS_ERR_INVALID_ARG;
+        if (x.method < RS_NEAREST || x.method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
+        if (x.src_pitch < (int64_t)x.W * x.C || x.dst_pitch < (int64_t)x.Wo * x.C) return RS_ERR_INVALID_ARG;
+        if (reinterpret_cast<uintptr_t>(x.src) % es || reinterpret_cast<uintptr_t>(x.dst) % es)
+            return RS_ERR_ALIGNMENT;
+        Geom g;
+        g.H = x.H; g.W = x.W; g.Ho = x.Ho; g.Wo = x.Wo; g.C = x.C;
+        g.src_pitch = x.src_pitch; g.dst_pitch = x.dst_pitch;
+        g.sp = PlaneMap{0, 0, 1}; g.dp = PlaneMap{0, 0, 1};
+        g.planes = 1; g.coord = o.coord; g.a = o.cubic_a;
+        TileCfg c;
+        if (!image_tile(g, x.method, tile_w, h_cap, threads, 72 * 1024, c)) return RS_ERR_UNSUPPORTED;
+        BatchImage& im = g_noalloc_imgs[k];
+        std::memset(&im, 0, sizeof im);
+        im.src = x.src; im.dst = x.dst;
+        im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
+        im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
+        im.tile_w = c.tile_w; im.tile_h = c.tile_h; im.sh_max = c.sh_max; im.swe_max = c.swe_max;
+        im.tiles_x = (int)(((int64_t)x.Wo * x.C + c.tile_w - 1) / c.tile_w);
+        g_noalloc_start[k + 1] = g_noalloc_start[k] + (int64_t)im.tiles_x * ((x.Ho + c.tile_h - 1) / c.tile_h);
+        smem = std::max(smem, c.smem);
+    }
+    for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) {
+            if (overlaps(d[k].dst, dst_bytes(d[k]), d[l].src, src_bytes(d[l]))) return RS_ERR_INVALID_ARG;
+            if (l != k && overlaps(d[k].dst, dst_bytes(d[k]), d[l].dst, dst_bytes(d[l]))) return RS_ERR_INVALID_ARG;
+        }
+    return RS_OK;
+}
+
 }  // namespace rs
+
+extern "C" rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs_dtype dtype, const rs_options* opt,
+                                               void* stream)
+{
+    using namespace rs;
+    const rs_options o = options_or_default(opt);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    size_t smem = 0;
+    int threads = 256;
+    rs_status s = noalloc_prepare(d, n, dtype, o, smem, threads);
+    if (s != RS_OK) return s;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return RS_ERR_UNSUPPORTED;
+    if (!g_noalloc_dev[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_batch_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_noalloc_dev[dev] = p;
+    }
+    char* scratch = static_cast<char*>(g_noalloc_dev[dev]);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Pageable source: each copy returns once the host data has been staged,
+    // so the staging arrays may be refilled by the next call.
+    e = cudaMemcpyAsync(scratch, g_noalloc_imgs, sizeof(BatchImage) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scratch + kNoAllocImgBytes, g_noalloc_start, sizeof(int64_t) * (size_t)(n + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    void* func = batched_kernel(dtype);
+    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return cuda_status(e);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem)) != cudaSuccess)
+        return cuda_status(e);
+    const int64_t total = g_noalloc_start[n];
+    const int64_t blocks = std::min<int64_t>(total, (int64_t)num_sms() * std::max(1, per_sm));
+    const BatchImage* imgs = reinterpret_cast<const BatchImage*>(scratch);
+    const int64_t* start = reinterpret_cast<const int64_t*>(scratch + kNoAllocImgBytes);
+    int nn = n, coord = o.coord;
+    float a = o.cubic_a;
+    int64_t tot = total;
+    unsigned int* fw = fault_word();
+    void* args[] = {&imgs, &start, &nn, &tot, &coord, &a, &fw};
+    e = cudaLaunchKernel(func, dim3((unsigned)std::max<int64_t>(1, blocks)), dim3(threads), args, smem, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_status(e);
+}
 
 using namespace rs;
 
