@@ -61,8 +61,16 @@ typedef enum { RS_NEAREST = 0, RS_BILINEAR = 1, RS_BICUBIC = 2 } rs_method;
 typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
 
 /* Kernel selection.
- * AUTO   = the tuned (or default) kernel for the problem: the streaming
- *          kernel when its footprint fits in shared memory, else TILED.
+ * AUTO   = the tuned (or default) kernel for the problem: GATHER for
+ *          RS_NEAREST; WINDOW for bilinear / bicubic when its footprint fits
+ *          in shared memory, else STREAM, else TILED.
+ * WINDOW = bilinear / bicubic: each thread owns 4 output elements of a
+ *          1024-element strip for a whole band of rows and keeps the
+ *          horizontally interpolated source rows its taps need in registers,
+ *          so each output row is blended without touching shared memory;
+ *          source rows are staged in chunks of tile_h rows (double
+ *          buffered, next chunk's loads in flight); waves = blocks per
+ *          resident block slot (sets the band height).
  * STREAM = one block per (column strip, band of rows), walking down the band
  *          in chunks; every source row is staged and horizontally
  *          interpolated once per strip; loads of the next chunk are issued
@@ -71,10 +79,15 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
  *          block slot (sets the band height).
  * TILED  = one block per output tile of tile_w elements x tile_h rows with
  *          `threads` threads; the footprint and halo are staged per tile.
+ * GATHER = RS_NEAREST only (AUTO's choice for it): a bit-exact gather, each
+ *          thread copying 16 bytes of a strip of tile_w output elements over
+ *          tile_h consecutive output rows, reusing a gathered row for the
+ *          next output row when both map to the same source row.
  * PLAIN  = one thread per output pixel reading its taps from global memory,
  *          thread blocks of tile_w x tile_h threads (default 32 x 4): the
  *          paper's kernel (Sec. III.A, Eq. 6), kept as the comparison row. */
-typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_STREAM = 3 } rs_impl;
+typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_STREAM = 3,
+               RS_IMPL_GATHER = 4, RS_IMPL_WINDOW = 5 } rs_impl;
 
 typedef struct {
     int32_t coord;      /* rs_coord; default RS_COORD_ASYMMETRIC */
@@ -233,7 +246,7 @@ rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
  * The cache can be saved to and loaded from a text file.
  */
 typedef struct {
-    int32_t impl;       /* RS_IMPL_STREAM or RS_IMPL_TILED */
+    int32_t impl;       /* RS_IMPL_WINDOW, RS_IMPL_STREAM, RS_IMPL_TILED or RS_IMPL_GATHER */
     int32_t tile_w, tile_h, threads, waves;
     float best_us;      /* measured time of the chosen configuration */
     float default_us;   /* measured time of the default configuration */

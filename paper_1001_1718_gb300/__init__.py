@@ -23,7 +23,7 @@ from ._binding import ResampleError, lib
 METHODS = {"nearest": B.RS_NEAREST, "bilinear": B.RS_BILINEAR, "bicubic": B.RS_BICUBIC}
 COORDS = {"asymmetric": B.RS_COORD_ASYMMETRIC, "half_pixel": B.RS_COORD_HALF_PIXEL}
 IMPLS = {"auto": B.RS_IMPL_AUTO, "tiled": B.RS_IMPL_TILED, "plain": B.RS_IMPL_PLAIN,
-         "stream": B.RS_IMPL_STREAM}
+         "stream": B.RS_IMPL_STREAM, "gather": B.RS_IMPL_GATHER, "window": B.RS_IMPL_WINDOW}
 IMPL_NAMES = {v: k for k, v in IMPLS.items()}
 DTYPES = {torch.uint8: B.RS_U8, torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16,
           torch.float32: B.RS_F32}
@@ -118,7 +118,8 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
            waves: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
     """Resample x to size (Ho, Wo). Same dtype out; FP32 arithmetic.
 
-    impl: "auto" (tuned or default kernel), "stream", "tiled" or "plain";
+    impl: "auto" (tuned or default kernel), "window", "stream", "tiled",
+    "plain" or "gather" (nearest only);
     tile = (tile_w, tile_h) and threads / waves override the kernel shape."""
     _require_cuda(x)
     Ho, Wo = int(size[0]), int(size[1])

@@ -44,6 +44,8 @@ static std::string tune_key(const Geom& g, int method, int dtype)
 
 static bool valid_tuned(const Tuned& t)
 {
+    if (t.impl == RS_IMPL_GATHER) return t.tile_w > 0 && t.tile_h > 0;
+    if (t.impl == RS_IMPL_WINDOW) return t.tile_h > 0 && t.waves > 0;
     if (t.impl == RS_IMPL_STREAM) return t.tile_w > 0 && t.tile_h > 0 && t.waves > 0;
     if (t.impl == RS_IMPL_TILED) return t.tile_w > 0 && t.tile_h > 0 && (t.threads == 128 || t.threads == 256);
     return false;
@@ -82,6 +84,17 @@ static void load_env_once()
 static bool make_choice(const Geom& g, int method, int dtype, const void* src, const Tuned& t, KernelChoice& k)
 {
     k.impl = t.impl;
+    if (t.impl == RS_IMPL_GATHER) {
+        k.gather_w = t.tile_w;
+        k.gather_rows = t.tile_h;
+        return method == RS_NEAREST && nearest_config(g, dtype, t.tile_w, t.tile_h);
+    }
+    if (t.impl == RS_IMPL_WINDOW) {
+        k.window = PolyCfg{};
+        k.window.chunk = t.tile_h;
+        k.window.waves = t.waves;
+        return poly_config(g, method, dtype, src, k.window);
+    }
     if (t.impl == RS_IMPL_STREAM) {
         k.stream = StreamCfg{};
         k.stream.tile_w = t.tile_w;
@@ -95,6 +108,15 @@ static bool make_choice(const Geom& g, int method, int dtype, const void* src, c
 
 static bool default_choice(const Geom& g, int method, int dtype, const void* src, KernelChoice& k)
 {
+    if (method == RS_NEAREST) {
+        // one warp per output row of the strip (512 bytes), 8 rows per thread
+        const Tuned t{RS_IMPL_GATHER, 32 * (16 / (int)dtype_size(dtype)), 8, 256, 0};
+        if (make_choice(g, method, dtype, src, t, k)) return true;
+    }
+    for (int ch : {8, 4}) {   // register window, 8-row chunks within ~100 KB
+        const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
+        if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= 100 * 1024) return true;
+    }
     StreamCfg sc = stream_default(g, method, dtype, src);
     if (sc.tile_w) {
         sc.waves = 4;
@@ -111,6 +133,16 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
                         KernelChoice& k)
 {
     const bool explicit_shape = o.tile_w || o.tile_h || o.threads || o.waves;
+    if (o.impl == RS_IMPL_GATHER) {
+        const int ev = 16 / (int)dtype_size(dtype);
+        const Tuned t{RS_IMPL_GATHER, o.tile_w ? o.tile_w : 32 * ev, o.tile_h ? o.tile_h : 8, 256, 0};
+        if (method != RS_NEAREST) return RS_ERR_INVALID_ARG;
+        return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
+    }
+    if (o.impl == RS_IMPL_WINDOW) {
+        const Tuned t{RS_IMPL_WINDOW, 1024, o.tile_h ? o.tile_h : 8, 256, o.waves ? o.waves : 2};
+        return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
+    }
     if (o.impl == RS_IMPL_STREAM || (o.impl == RS_IMPL_AUTO && explicit_shape && !o.threads)) {
         StreamCfg d = stream_default(g, method, dtype, src);
         Tuned t{RS_IMPL_STREAM, o.tile_w ? o.tile_w : (d.tile_w ? d.tile_w : 512),
@@ -140,6 +172,8 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
 cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src, void* dst, const KernelChoice& k,
                           cudaStream_t st)
 {
+    if (k.impl == RS_IMPL_GATHER) return launch_nearest(g, dtype, src, dst, k.gather_w, k.gather_rows, st);
+    if (k.impl == RS_IMPL_WINDOW) return launch_poly(g, method, dtype, src, dst, k.window, st);
     if (k.impl == RS_IMPL_STREAM) return launch_stream(g, method, dtype, src, dst, k.stream, st);
     return launch_tiled(g, method, dtype, src, dst, k.tile, st);
 }
@@ -174,6 +208,8 @@ static cudaError_t time_choice(const Geom& g, int method, int dtype, const void*
 
 static Tuned to_tuned(const KernelChoice& k)
 {
+    if (k.impl == RS_IMPL_GATHER) return Tuned{RS_IMPL_GATHER, k.gather_w, k.gather_rows, 256, 0};
+    if (k.impl == RS_IMPL_WINDOW) return Tuned{RS_IMPL_WINDOW, 1024, k.window.chunk, 256, k.window.waves};
     if (k.impl == RS_IMPL_STREAM) return Tuned{RS_IMPL_STREAM, k.stream.tile_w, k.stream.chunk_h, 256, k.stream.waves};
     return Tuned{RS_IMPL_TILED, k.tile.tile_w, k.tile.tile_h, k.tile.threads, 0};
 }
@@ -202,12 +238,19 @@ rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_
     if (s != RS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<Tuned> cands;
+    for (int ch : {4, 8, 16})
+        for (int wv : {1, 2, 4}) cands.push_back(Tuned{RS_IMPL_WINDOW, 1024, ch, 256, wv});
     for (int tw : {128, 256, 512, 1024})
         for (int ch : {4, 8, 16, 32})
             for (int wv : {2, 4, 8}) cands.push_back(Tuned{RS_IMPL_STREAM, tw, ch, 256, wv});
     for (int tw : {128, 256, 512, 1024})
         for (int th : {4, 8, 16, 32, 64})
             for (int nt : {128, 256}) cands.push_back(Tuned{RS_IMPL_TILED, tw, th, nt, 0});
+    if (method == RS_NEAREST) {
+        const int ev = 16 / (int)dtype_size(dtype);
+        for (int nv : {8, 16, 32, 64, 128, 256})
+            for (int rows : {1, 2, 4, 8, 16}) cands.push_back(Tuned{RS_IMPL_GATHER, nv * ev, rows, 256, 0});
+    }
     KernelChoice def;
     if (!default_choice(g, method, dtype, src, def)) return RS_ERR_UNSUPPORTED;
     float def_us = 0.0f;

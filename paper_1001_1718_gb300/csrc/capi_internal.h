@@ -25,9 +25,11 @@ rs_status make_geom(const void* src, const rs_layout* in, const void* dst, const
 // Kernel and configuration for a forward call: explicit options, else the
 // tuning cache, else the default (streaming kernel when it fits).
 struct KernelChoice {
-    int impl;        // RS_IMPL_STREAM or RS_IMPL_TILED
+    int impl;        // RS_IMPL_STREAM, RS_IMPL_TILED or RS_IMPL_GATHER
     TileCfg tile;
     StreamCfg stream;
+    int gather_w, gather_rows;   // RS_IMPL_GATHER: strip width, rows per thread
+    PolyCfg window;              // RS_IMPL_WINDOW
 };
 rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, const rs_options& o,
                         KernelChoice& k);

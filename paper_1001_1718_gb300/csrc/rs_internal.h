@@ -67,6 +67,15 @@ struct StreamCfg {
     size_t smem;
 };
 
+// Configuration of the register-window kernel (bilinear / bicubic): strips
+// of 1024 output elements, bands of band_h output rows (0 = from occupancy
+// and `waves`), source rows staged in chunks of `chunk` rows (double
+// buffered) of swe_max elements; vec = 16-byte loads.
+struct PolyCfg {
+    int chunk, band_h, waves, swe_max, band_cap, vec;
+    size_t smem;
+};
+
 int method_taps(int method);
 size_t dtype_size(int dtype);
 
@@ -89,6 +98,12 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
 StreamCfg stream_default(const Geom& g, int method, int dtype, const void* src);
 cudaError_t launch_stream(const Geom& g, int method, int dtype, const void* src, void* dst, StreamCfg c,
                           cudaStream_t st);
+bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c);
+cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c,
+                        cudaStream_t st);
+bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread);
+cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst, int tile_w, int rows_per_thread,
+                           cudaStream_t st);
 cudaError_t launch_plain(const Geom& g, int method, int dtype, const void* src, void* dst,
                          int bw, int bh, cudaStream_t st);
 

@@ -84,6 +84,48 @@ __device__ __forceinline__ void store4v(T* p, float2 a, float2 b, int cnt)
         if (k < cnt) Store<T>::put(p + k, v[k]);
 }
 
+// Position of strip element e in a padded ring row (4 floats per 16).
+__device__ __forceinline__ int hpos(int e) { return e + ((e >> 4) << 2); }
+
+// Store EV = 16 / sizeof(T) consecutive elements (the first `cnt`) given as
+// float pairs: one 16-byte store when all are in range and the address is
+// 16-byte aligned, else groups of four.
+template <typename T>
+__device__ __forceinline__ void store16(T* p, const float2* v, int cnt)
+{
+    constexpr int EV = 16 / (int)sizeof(T);
+    if (cnt == EV && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        uint4 w;
+        if constexpr (sizeof(T) == 1) {
+            w.x = pack_u8x4(v[0], v[1]);
+            w.y = pack_u8x4(v[2], v[3]);
+            w.z = pack_u8x4(v[4], v[5]);
+            w.w = pack_u8x4(v[6], v[7]);
+        } else if constexpr (sizeof(T) == 2) {
+            uint32_t h[4];
+            #pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (std::is_same<T, __half>::value) {
+                    __half2 x = __float22half2_rn(v[k]);
+                    h[k] = *reinterpret_cast<uint32_t*>(&x);
+                } else {
+                    __nv_bfloat162 x = __float22bfloat162_rn(v[k]);
+                    h[k] = *reinterpret_cast<uint32_t*>(&x);
+                }
+            }
+            w = make_uint4(h[0], h[1], h[2], h[3]);
+        } else {
+            w = make_uint4(__float_as_uint(v[0].x), __float_as_uint(v[0].y), __float_as_uint(v[1].x),
+                           __float_as_uint(v[1].y));
+        }
+        *reinterpret_cast<uint4*>(p) = w;
+        return;
+    }
+    #pragma unroll
+    for (int gq = 0; gq < EV / 4; ++gq)
+        if (cnt > 4 * gq) store4v<T>(p + 4 * gq, v[2 * gq], v[2 * gq + 1], min(4, cnt - 4 * gq));
+}
+
 // 16 bytes of storage -> FP32 in shared memory (4 / 8 / 16 elements).
 template <typename T>
 __device__ __forceinline__ void unpack16(const uint4& u, float* dst)
@@ -168,9 +210,12 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
         return;
     }
 
+    // Ring rows are padded by 4 floats per 16 elements, so the 16-byte
+    // accesses of both passes spread over the shared-memory banks.
+    const int HRS = TWE + TWE / 4;                         // ring row stride
     float* SR = sm;                                        // [rs_rows][swe_max]
-    float* HR = SR + cfg.rs_rows * cfg.swe_max;            // [rh][TWE]
-    float* RW = HR + cfg.rh * TWE;                         // [band_cap][KT]
+    float* HR = SR + cfg.rs_rows * cfg.swe_max;            // [rh][HRS]
+    float* RW = HR + cfg.rh * HRS;                         // [band_cap][KT]
     int* RB = reinterpret_cast<int*>(RW + cfg.band_cap * KT);      // [band_cap]
     const int hmask = cfg.rh - 1;
     if (ye - yb > cfg.band_cap) {   // uniform; the host sizes the table for the band
@@ -366,35 +411,59 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
                     h23 = __ffma2_rn(w23[q], make_float2(Sr[off[2] + q * C], Sr[off[3] + q * C]), h23);
                 }
                 const int slot = (n_lo + k + kRowBias) & hmask;
-                *reinterpret_cast<float4*>(HR + slot * TWE + 4 * qx) = make_float4(h01.x, h01.y, h23.x, h23.y);
+                *reinterpret_cast<float4*>(HR + slot * HRS + hpos(4 * qx)) = make_float4(h01.x, h01.y, h23.x, h23.y);
             }
         }
         __syncthreads();
 
-        // Vertical pass and store.
-        if (4 * qx < nE) {
-            const int cnt = min(4, nE - 4 * qx);
-            for (int i = ty; i < nR; i += rpp) {
-                const int code = rb[i];
-                const int f = (code >> 1);             // biased first tap row
-                float2 v01, v23;
-                if (code & 1) {
-                    const int slot = (f + (KT == 4 ? 1 : 0)) & hmask;
-                    const float4 hv = *reinterpret_cast<const float4*>(HR + slot * TWE + 4 * qx);
-                    v01 = make_float2(hv.x, hv.y);
-                    v23 = make_float2(hv.z, hv.w);
-                } else {
-                    v01 = make_float2(0.0f, 0.0f);
-                    v23 = make_float2(0.0f, 0.0f);
-                    #pragma unroll
-                    for (int p = 0; p < KT; ++p) {
-                        const float wy = rw[i * KT + p];
-                        const float4 hv = *reinterpret_cast<const float4*>(HR + ((f + p) & hmask) * TWE + 4 * qx);
-                        v01 = __ffma2_rn(make_float2(wy, wy), make_float2(hv.x, hv.y), v01);
-                        v23 = __ffma2_rn(make_float2(wy, wy), make_float2(hv.z, hv.w), v23);
+        // Vertical pass and store: each thread writes 16 bytes (EV
+        // consecutive elements) of one output row per iteration.
+        {
+            constexpr int EV = 16 / (int)sizeof(T);
+            constexpr int NG = EV / 4;
+            const int nv = TWE / EV, vpp = kThreads / nv;
+            const int vx = tid % nv, vy = tid / nv;
+            const int ev0 = EV * vx;
+            if (ev0 < nE) {
+                const int cnt = min(EV, nE - ev0);
+                const int hoff = hpos(ev0);
+                for (int i = vy; i < nR; i += vpp) {
+                    const int code = rb[i];
+                    const int f = code >> 1;             // biased first tap row
+                    float2 v[2 * NG];
+                    if (code & 1) {
+                        const float* hr = HR + ((f + (KT == 4 ? 1 : 0)) & hmask) * HRS + hoff;
+                        #pragma unroll
+                        for (int gq = 0; gq < NG; ++gq) {
+                            const float4 hv = *reinterpret_cast<const float4*>(hr + 4 * gq);
+                            v[2 * gq] = make_float2(hv.x, hv.y);
+                            v[2 * gq + 1] = make_float2(hv.z, hv.w);
+                        }
+                    } else {
+                        float wy[KT];
+                        if constexpr (KT == 4) {
+                            const float4 w4 = *reinterpret_cast<const float4*>(rw + i * 4);
+                            wy[0] = w4.x; wy[1] = w4.y; wy[2] = w4.z; wy[3] = w4.w;
+                        } else {
+                            #pragma unroll
+                            for (int p = 0; p < KT; ++p) wy[p] = rw[i * KT + p];
+                        }
+                        #pragma unroll
+                        for (int gq = 0; gq < 2 * NG; ++gq) v[gq] = make_float2(0.0f, 0.0f);
+                        #pragma unroll
+                        for (int p = 0; p < KT; ++p) {
+                            const float2 w2 = make_float2(wy[p], wy[p]);
+                            const float* hr = HR + ((f + p) & hmask) * HRS + hoff;
+                            #pragma unroll
+                            for (int gq = 0; gq < NG; ++gq) {
+                                const float4 hv = *reinterpret_cast<const float4*>(hr + 4 * gq);
+                                v[2 * gq] = __ffma2_rn(w2, make_float2(hv.x, hv.y), v[2 * gq]);
+                                v[2 * gq + 1] = __ffma2_rn(w2, make_float2(hv.z, hv.w), v[2 * gq + 1]);
+                            }
+                        }
                     }
+                    store16<T>(d + (int64_t)(y + i) * g.dst_pitch + e0 + ev0, v, cnt);
                 }
-                store4v<T>(d + (int64_t)(y + i) * g.dst_pitch + e0 + 4 * qx, v01, v23, cnt);
             }
         }
         n_lo = nx_lo;
@@ -423,7 +492,10 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
 {
     const int KT = method_taps(method);
     const int es = (int)dtype_size(dtype);
-    if (c.tile_w < 4 || (c.tile_w & 3) || c.tile_w / 4 > kThreads || kThreads % (c.tile_w / 4)) return false;
+    // strips of a multiple of 16 elements: 4 per thread in the horizontal
+    // pass, 16 bytes per thread in the vertical pass
+    if (c.tile_w < 16 || (c.tile_w & 15) || c.tile_w / 4 > kThreads || kThreads % (c.tile_w / 4)) return false;
+    if (c.tile_w / (16 / es) > kThreads || kThreads % (c.tile_w / (16 / es))) return false;
     if (c.chunk_h < 1) return false;
     // 16-byte units need every staged row to start and end on 16 bytes.
     const uintptr_t base = reinterpret_cast<uintptr_t>(src);
@@ -443,7 +515,7 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
     const int chunks_cap = std::max(1, kMaxBand / c.chunk_h);
     c.band_cap = (int)std::min<int64_t>((int64_t)chunks_cap * c.chunk_h,
                                         ((int64_t)g.Ho + c.chunk_h - 1) / c.chunk_h * c.chunk_h);
-    c.smem = sizeof(float) * ((size_t)c.rs_rows * c.swe_max + (size_t)c.rh * c.tile_w +
+    c.smem = sizeof(float) * ((size_t)c.rs_rows * c.swe_max + (size_t)c.rh * (c.tile_w + c.tile_w / 4) +
                               (size_t)c.band_cap * KT) +
              sizeof(int) * (size_t)c.band_cap;
     return c.smem <= max_smem_per_block();

@@ -192,16 +192,64 @@ def test_stream_kernel_configs(rs, oracle, cfg, dtype):
     assert rs.debug_fault() == 0
 
 
-@pytest.mark.parametrize("impl", ["stream", "tiled", "plain"])
+@pytest.mark.parametrize("impl", ["stream", "tiled", "plain", "window", "gather"])
 def test_kernels_agree_bitwise(rs, impl):
     """Every kernel computes each output element with the same FP32
     operations in the same order (horizontal taps, then vertical), so they
-    agree bit for bit."""
+    agree bit for bit (the gather kernel only does nearest, the register
+    window kernel only bilinear / bicubic)."""
     x = torch.randint(0, 256, (333, 517, 3), dtype=torch.uint8, device="cuda")
     xf = torch.randn(2, 3, 190, 260, device="cuda")
-    for method in ("bilinear", "bicubic", "nearest"):
+    methods = {"gather": ("nearest",), "window": ("bilinear", "bicubic")}.get(
+        impl, ("bilinear", "bicubic", "nearest"))
+    for method in methods:
         ref = rs.resize(x, (701, 911), method, impl="tiled")
         assert torch.equal(rs.resize(x, (701, 911), method, impl=impl), ref)
         reff = rs.resize(xf, (97, 555), method, layout="nchw", impl="tiled")
         got = rs.resize(xf, (97, 555), method, layout="nchw", impl=impl)
         assert torch.equal(got, reff)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+@pytest.mark.parametrize("cfg", [(None, 0), ((16, 1), 0), ((64, 4), 0), ((1024, 2), 0), ((256, 16), 0)])
+def test_gather_kernel_nearest(rs, oracle, dtype, cfg):
+    """The nearest-neighbour gather kernel is bit-exact against the oracle at
+    several strip widths / rows per thread (strip widths are in elements and
+    are rounded to the kernel's 16-byte unit by the caller)."""
+    tile, _ = cfg
+    ev = {"u8": 16, "f16": 8, "f32": 4}[dtype]
+    if tile is not None:
+        tile = (max(ev, (tile[0] // ev) * ev), tile[1])
+    for k, (H, W, C, Ho, Wo, coord) in enumerate([(100, 130, 3, 200, 260, 0), (77, 91, 1, 160, 33, 1),
+                                                   (256, 256, 4, 128, 512, 0), (9, 1000, 3, 31, 1999, 1)]):
+        t, x64 = _src(500 + k, (H, W, C), dtype)
+        y = rs.resize(t.cuda(), (Ho, Wo), "nearest", coord=CNAME[coord], impl="gather", tile=tile)
+        torch.cuda.synchronize()
+        check(y, oracle.resize(x64, Ho, Wo, NN, coord), dtype, NN, 1.0, f"gather {cfg} {dtype}")
+        assert torch.equal(y, rs.resize(t.cuda(), (Ho, Wo), "nearest", coord=CNAME[coord], impl="tiled"))
+
+
+@pytest.mark.parametrize("cfg", [(8, 2), (4, 1), (16, 4), (4, 8)])
+@pytest.mark.parametrize("dtype", ["u8", "f32", "f16"])
+def test_window_kernel_configs(rs, oracle, cfg, dtype):
+    """The register-window kernel at several chunk heights and band counts,
+    on 16-byte rows and odd rows, up- and downscale, both coordinate maps."""
+    chunk, waves = cfg
+    for k, (H, W, C, Ho, Wo, method, coord) in enumerate([
+            (160, 512, 4, 321, 1024, BC, 0),
+            (157, 203, 3, 301, 391, BC, 1),
+            (96, 128, 1, 173, 250, BL, 0),
+            (200, 160, 3, 99, 81, BC, 0),
+            (31, 700, 1, 62, 1399, BL, 1),
+            (2, 3, 3, 7, 5, BC, 0)]):
+        t, x64 = _src(700 + k, (H, W, C), dtype)
+        try:
+            y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], coord=CNAME[coord], impl="window",
+                          tile=(1024, chunk), waves=waves)
+        except rs.ResampleError as e:
+            assert e.status == 1 and Ho < H          # downscale footprint too large for the chunk
+            continue
+        torch.cuda.synchronize()
+        check(y, oracle.resize(x64, Ho, Wo, method, coord), dtype, method, np.abs(x64).max(),
+              f"window {cfg} {dtype} {H}x{W}x{C}->{Ho}x{Wo}")
+    assert rs.debug_fault() == 0
