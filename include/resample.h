@@ -204,7 +204,7 @@ rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype,
  *
  * The work list goes into a fixed array of device memory declared inside
  * the library (static __device__, RS_NOALLOC_MAX_IMAGES descriptors, about
- * 352 KB); every GPU that loads the library holds it until the process
+ * 480 KB); every GPU that loads the library holds it until the process
  * exits. Nothing is allocated: no cudaMalloc, cudaFree or allocating library
  * routine is called.
  *   - n > RS_NOALLOC_MAX_IMAGES returns RS_ERR_WORKSPACE, before any work.

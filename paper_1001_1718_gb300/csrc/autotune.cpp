@@ -109,8 +109,8 @@ static bool make_choice(const Geom& g, int method, int dtype, const void* src, c
 static bool default_choice(const Geom& g, int method, int dtype, const void* src, KernelChoice& k)
 {
     if (method == RS_NEAREST) {
-        // one warp per output row of the strip (512 bytes), 8 rows per thread
-        const Tuned t{RS_IMPL_GATHER, 32 * (16 / (int)dtype_size(dtype)), 8, 256, 0};
+        // 64 threads per output row of the strip (1 KB), 16 rows per thread
+        const Tuned t{RS_IMPL_GATHER, 64 * (16 / (int)dtype_size(dtype)), 16, 256, 0};
         if (make_choice(g, method, dtype, src, t, k)) return true;
     }
     for (int ch : {8, 4}) {   // register window, 8-row chunks within ~100 KB
@@ -135,7 +135,7 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
     const bool explicit_shape = o.tile_w || o.tile_h || o.threads || o.waves;
     if (o.impl == RS_IMPL_GATHER) {
         const int ev = 16 / (int)dtype_size(dtype);
-        const Tuned t{RS_IMPL_GATHER, o.tile_w ? o.tile_w : 32 * ev, o.tile_h ? o.tile_h : 8, 256, 0};
+        const Tuned t{RS_IMPL_GATHER, o.tile_w ? o.tile_w : 64 * ev, o.tile_h ? o.tile_h : 16, 256, 0};
         if (method != RS_NEAREST) return RS_ERR_INVALID_ARG;
         return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
     }

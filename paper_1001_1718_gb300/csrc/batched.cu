@@ -1,14 +1,21 @@
 // Ragged batch: many images of uneven sizes, each with its own scale,
-// channel count and method, resampled by one persistent kernel launch.
+// channel count and method, resampled by persistent kernels that walk a
+// work list in device memory.
 //
-// The host cuts every image into output tiles (tile_w elements x tile_h
-// rows, tile_h chosen per image so the staged footprint fits the block's
-// shared memory), lays the images' tile counts out as an exclusive prefix
-// sum, and uploads the descriptors and the prefix into the caller's
-// workspace. The kernel runs one block per resident slot (SM count x blocks
-// per SM); block b takes tiles b, b + gridDim.x, ..., finds each tile's image
-// by binary search in the prefix and runs the same tile_body as the
-// single-image kernel. No block waits on another.
+// The host sorts the images into classes. A bilinear / bicubic image whose
+// footprint fits becomes (strip of 1024 output elements, band of output
+// rows) items of the register-window kernel, in the class of its (method,
+// channel count); any other image (nearest, or too large a footprint)
+// becomes output tiles of the tiled kernel, in one class of its own. Each
+// class is a contiguous run of image descriptors with an exclusive prefix
+// sum of their item counts; descriptors and prefixes go to device memory
+// (the caller's workspace, or the library's fixed array for the
+// no-allocation entry point). Each non-empty class is ONE persistent launch,
+// fully specialised for its class: one block per resident slot (SM count x
+// blocks per SM); block b takes items b, b + gridDim.x, ..., finds each
+// item's image by binary search in the class prefix and runs the image's
+// per-block work. No block waits on another. The replayable plan records the
+// class launches as independent nodes of one CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -17,6 +24,7 @@
 #include <vector>
 
 #include "capi_internal.h"
+#include "poly_body.cuh"
 #include "tile_body.cuh"
 
 namespace rs {
@@ -26,9 +34,69 @@ struct BatchImage {
     void* dst;
     int64_t src_pitch, dst_pitch;
     int H, W, Ho, Wo;
-    int C, method, tiles_x, pad;
-    int tile_w, tile_h, sh_max, swe_max;
+    int C, method, tiles_x, kind;          // tiles_x: items per row of items; kind 0 tile, 1 window
+    int tile_w, tile_h, sh_max, swe_max;   // kind 0: tiled-kernel tile
+    int chunk, band_h, w_swe_max, band_cap, pos_cap, vec, pad0, pad1;   // kind 1: window config
 };
+
+// Classes: 0..7 = window (KT 2 / 4) x (C 1..4), 8 = tiled.
+static constexpr int kClasses = 9;
+static constexpr int kTileClass = 8;
+
+__device__ __forceinline__ int find_image(const int64_t* __restrict__ start, int n, int64_t t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ Geom image_geom(const BatchImage& im, int coord, float a)
+{
+    Geom g;
+    g.H = im.H; g.W = im.W; g.Ho = im.Ho; g.Wo = im.Wo; g.C = im.C;
+    g.src_pitch = im.src_pitch;
+    g.dst_pitch = im.dst_pitch;
+    g.sp = PlaneMap{0, 0, 1};
+    g.dp = PlaneMap{0, 0, 1};
+    g.planes = 1;
+    g.coord = coord;
+    g.a = a;
+    return g;
+}
+
+// Window items of one (KT, C) class.
+template <int KT, int C, typename T>
+__global__ void __launch_bounds__(256, 3)
+k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start, int n, int64_t total,
+                 int coord, float a, unsigned int* fault)
+{
+    extern __shared__ __align__(16) float sm[];
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int k = find_image(start, n, t);
+        const BatchImage im = imgs[k];
+        const int64_t local = t - __ldg(start + k);
+        if (local < 0 || local >= __ldg(start + k + 1) - __ldg(start + k) || im.kind != 1 || im.C != C) {
+            if (threadIdx.x == 0) report_fault(fault, FAULT_BATCH_INDEX);   // uniform over the block
+            continue;
+        }
+        const Geom g = image_geom(im, coord, a);
+        PolyCfg pc;
+        pc.chunk = im.chunk;
+        pc.band_h = im.band_h;
+        pc.waves = 0;
+        pc.swe_max = im.w_swe_max;
+        pc.band_cap = im.band_cap;
+        pc.pos_cap = im.pos_cap;
+        pc.vec = im.vec;
+        pc.smem = 0;
+        poly_body<KT, C, T>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), pc,
+                            (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
+        __syncthreads();   // the next item reuses shared memory
+    }
+}
 
 template <int KT, typename T>
 __device__ __forceinline__ void batch_tile_c(const Geom& g, const BatchImage& im, const TileCfg& cfg, int bx,
@@ -44,6 +112,7 @@ __device__ __forceinline__ void batch_tile_c(const Geom& g, const BatchImage& im
     }
 }
 
+// Tile items of any method and channel count.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_batched(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start, int n, int64_t total,
@@ -51,28 +120,14 @@ k_batched(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start
 {
     extern __shared__ __align__(16) float sm[];
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        // image k with start[k] <= t < start[k + 1]
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(start + mid) <= t) lo = mid; else hi = mid - 1;
-        }
-        const BatchImage im = imgs[lo];
-        const int64_t local = t - __ldg(start + lo);
-        const int64_t count = __ldg(start + lo + 1) - __ldg(start + lo);
-        if (local < 0 || local >= count) {   // uniform over the block
-            if (threadIdx.x == 0) report_fault(fault, FAULT_BATCH_INDEX);
+        const int k = find_image(start, n, t);
+        const BatchImage im = imgs[k];
+        const int64_t local = t - __ldg(start + k);
+        if (local < 0 || local >= __ldg(start + k + 1) - __ldg(start + k) || im.kind != 0) {
+            if (threadIdx.x == 0) report_fault(fault, FAULT_BATCH_INDEX);   // uniform over the block
             continue;
         }
-        Geom g;
-        g.H = im.H; g.W = im.W; g.Ho = im.Ho; g.Wo = im.Wo; g.C = im.C;
-        g.src_pitch = im.src_pitch;
-        g.dst_pitch = im.dst_pitch;
-        g.sp = PlaneMap{0, 0, 1};
-        g.dp = PlaneMap{0, 0, 1};
-        g.planes = 1;
-        g.coord = coord;
-        g.a = a;
+        const Geom g = image_geom(im, coord, a);
         TileCfg cfg;
         cfg.tile_w = im.tile_w;
         cfg.tile_h = im.tile_h;
@@ -94,16 +149,6 @@ k_batched(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start
 // Host side
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-struct BatchPlanHost {
-    std::vector<BatchImage> imgs;
-    std::vector<int64_t> start;
-    size_t smem = 0;
-    int threads = 256;
-    size_t ws_bytes = 0;
-    size_t off_start = 0;
-};
-
 static bool dim_ok(int v) { return v >= 1 && v <= 65535; }
 
 // Tile shape of one image: tile_w elements, the tallest tile_h <= h_cap that
@@ -122,77 +167,158 @@ static bool image_tile(const Geom& g, int method, int tile_w, int h_cap, int thr
     return false;
 }
 
-static rs_status batch_prepare(const rs_image_desc* d, int n, int dtype, const rs_options& o, BatchPlanHost& P)
+// Validates one descriptor and fills its device descriptor: window items
+// (bilinear / bicubic, footprint within ~100 KB of shared memory, default
+// shapes) or tiles. Returns the class, item count and shared-memory need.
+static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_options& o, int tile_w, int h_cap,
+                               int threads, BatchImage& im, int& cls, int64_t& items, size_t& smem)
 {
-    if (!d || n < 1 || n > (1 << 20)) return RS_ERR_INVALID_ARG;
+    const int64_t es = (int64_t)dtype_size(dtype);
+    if (!x.src || !x.dst) return RS_ERR_INVALID_ARG;
+    if (!dim_ok(x.H) || !dim_ok(x.W) || !dim_ok(x.Ho) || !dim_ok(x.Wo)) return RS_ERR_INVALID_ARG;
+    if (x.C < 1 || x.C > 4) return RS_ERR_INVALID_ARG;
+    if (x.method < RS_NEAREST || x.method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
+    if (x.src_pitch < (int64_t)x.W * x.C || x.dst_pitch < (int64_t)x.Wo * x.C) return RS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(x.src) % es || reinterpret_cast<uintptr_t>(x.dst) % es)
+        return RS_ERR_ALIGNMENT;
+    Geom g;
+    g.H = x.H; g.W = x.W; g.Ho = x.Ho; g.Wo = x.Wo; g.C = x.C;
+    g.src_pitch = x.src_pitch; g.dst_pitch = x.dst_pitch;
+    g.sp = PlaneMap{0, 0, 1}; g.dp = PlaneMap{0, 0, 1};
+    g.planes = 1; g.coord = o.coord; g.a = o.cubic_a;
+    std::memset(&im, 0, sizeof im);
+    im.src = x.src; im.dst = x.dst;
+    im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
+    im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
+    if (x.method != RS_NEAREST && !o.tile_w && !o.tile_h && !o.threads) {
+        for (int ch : {8, 4}) {
+            PolyCfg pc{};
+            pc.chunk = ch;
+            if (!poly_config(g, x.method, dtype, x.src, pc) || pc.smem > 100 * 1024) continue;
+            im.kind = 1;
+            im.chunk = pc.chunk;
+            im.band_h = std::min(pc.band_cap, 256);
+            im.w_swe_max = pc.swe_max;
+            im.band_cap = pc.band_cap;
+            im.pos_cap = pc.pos_cap;
+            im.vec = pc.vec;
+            im.tiles_x = (int)(((int64_t)x.Wo * x.C + 1023) / 1024);
+            items = (int64_t)im.tiles_x * ((x.Ho + im.band_h - 1) / im.band_h);
+            smem = pc.smem;
+            cls = (x.method == RS_BILINEAR ? 0 : 4) + (x.C - 1);
+            return RS_OK;
+        }
+    }
+    TileCfg c;
+    if (!image_tile(g, x.method, tile_w, h_cap, threads, 72 * 1024, c)) return RS_ERR_UNSUPPORTED;
+    im.kind = 0;
+    im.tile_w = c.tile_w; im.tile_h = c.tile_h; im.sh_max = c.sh_max; im.swe_max = c.swe_max;
+    im.tiles_x = (int)(((int64_t)x.Wo * x.C + c.tile_w - 1) / c.tile_w);
+    items = (int64_t)im.tiles_x * ((x.Ho + c.tile_h - 1) / c.tile_h);
+    smem = c.smem;
+    cls = kTileClass;
+    return RS_OK;
+}
+
+// Work-list layout shared by the workspace and the fixed-array paths:
+// descriptors grouped by class (class c occupies [first[c], first[c] +
+// count[c])), then per class an exclusive prefix of count[c] + 1 entries
+// starting at prefix[c] (an index into the int64 prefix area).
+struct BatchLayout {
+    int count[kClasses], first[kClasses], prefix[kClasses];
+    int64_t total[kClasses];
+    size_t smem[kClasses];
+    int threads;
+    int n;
+};
+
+// Fills imgs_out (n entries) and start_out (n + kClasses entries) grouped
+// by class, with no allocation (scratch arrays are caller-provided, n each).
+static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs_options& o, BatchImage* imgs_out,
+                              int64_t* start_out, BatchImage* tmp_imgs, int* tmp_cls, int64_t* tmp_items,
+                              BatchLayout& L)
+{
+    if (!d || n < 1) return RS_ERR_INVALID_ARG;
     if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
     rs_status s = check_options(o, RS_BILINEAR);
     if (s != RS_OK) return s;
     const int tile_w = o.tile_w ? o.tile_w : 512;
     const int h_cap = o.tile_h ? o.tile_h : 32;
-    P.threads = o.threads ? o.threads : 256;
-    if (P.threads != 128 && P.threads != 256) return RS_ERR_INVALID_ARG;
-    const size_t es = dtype_size(dtype);
-    std::vector<std::pair<const char*, int64_t>> srcs(n), dsts(n);
-    P.imgs.resize(n);
-    P.start.assign(n + 1, 0);
-    P.smem = 0;
+    L.threads = o.threads ? o.threads : 256;
+    if (L.threads != 128 && L.threads != 256) return RS_ERR_INVALID_ARG;
+    L.n = n;
+    for (int c = 0; c < kClasses; ++c) { L.count[c] = 0; L.total[c] = 0; L.smem[c] = 0; }
+    const int64_t es = (int64_t)dtype_size(dtype);
     for (int k = 0; k < n; ++k) {
-        const rs_image_desc& x = d[k];
-        if (!x.src || !x.dst) return RS_ERR_INVALID_ARG;
-        if (!dim_ok(x.H) || !dim_ok(x.W) || !dim_ok(x.Ho) || !dim_ok(x.Wo)) return RS_ERR_INVALID_ARG;
-        if (x.C < 1 || x.C > 4) return RS_ERR_INVALID_ARG;
-        if (x.method < RS_NEAREST || x.method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
-        if (x.src_pitch < (int64_t)x.W * x.C || x.dst_pitch < (int64_t)x.Wo * x.C) return RS_ERR_INVALID_ARG;
-        if (reinterpret_cast<uintptr_t>(x.src) % es || reinterpret_cast<uintptr_t>(x.dst) % es)
-            return RS_ERR_ALIGNMENT;
-        srcs[k] = {static_cast<const char*>(x.src), ((int64_t)(x.H - 1) * x.src_pitch + (int64_t)x.W * x.C) * (int64_t)es};
-        dsts[k] = {static_cast<const char*>(x.dst), ((int64_t)(x.Ho - 1) * x.dst_pitch + (int64_t)x.Wo * x.C) * (int64_t)es};
-        Geom g;
-        g.H = x.H; g.W = x.W; g.Ho = x.Ho; g.Wo = x.Wo; g.C = x.C;
-        g.src_pitch = x.src_pitch; g.dst_pitch = x.dst_pitch;
-        g.sp = PlaneMap{0, 0, 1}; g.dp = PlaneMap{0, 0, 1};
-        g.planes = 1; g.coord = o.coord; g.a = o.cubic_a;
-        TileCfg c;
-        if (!image_tile(g, x.method, tile_w, h_cap, P.threads, 72 * 1024, c)) return RS_ERR_UNSUPPORTED;
-        BatchImage& im = P.imgs[k];
-        std::memset(&im, 0, sizeof im);
-        im.src = x.src; im.dst = x.dst;
-        im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
-        im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
-        im.tile_w = c.tile_w; im.tile_h = c.tile_h; im.sh_max = c.sh_max; im.swe_max = c.swe_max;
-        im.tiles_x = (int)(((int64_t)x.Wo * x.C + c.tile_w - 1) / c.tile_w);
-        const int64_t tiles = (int64_t)im.tiles_x * ((x.Ho + c.tile_h - 1) / c.tile_h);
-        P.start[k + 1] = P.start[k] + tiles;
-        P.smem = std::max(P.smem, c.smem);
+        size_t sm = 0;
+        s = prepare_image(d[k], dtype, o, tile_w, h_cap, L.threads, tmp_imgs[k], tmp_cls[k], tmp_items[k], sm);
+        if (s != RS_OK) return s;
+        L.count[tmp_cls[k]]++;
+        L.smem[tmp_cls[k]] = std::max(L.smem[tmp_cls[k]], sm);
     }
     // No destination may overlap any source or another destination.
-    for (int k = 0; k < n; ++k) {
+    auto src_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.H - 1) * x.src_pitch + (int64_t)x.W * x.C) * es; };
+    auto dst_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.Ho - 1) * x.dst_pitch + (int64_t)x.Wo * x.C) * es; };
+    for (int k = 0; k < n; ++k)
         for (int l = 0; l < n; ++l) {
-            if (overlaps(dsts[k].first, dsts[k].second, srcs[l].first, srcs[l].second)) return RS_ERR_INVALID_ARG;
-            if (l != k && overlaps(dsts[k].first, dsts[k].second, dsts[l].first, dsts[l].second))
-                return RS_ERR_INVALID_ARG;
+            if (overlaps(d[k].dst, dst_bytes(d[k]), d[l].src, src_bytes(d[l]))) return RS_ERR_INVALID_ARG;
+            if (l != k && overlaps(d[k].dst, dst_bytes(d[k]), d[l].dst, dst_bytes(d[l]))) return RS_ERR_INVALID_ARG;
         }
+    int first = 0, pre = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        L.first[c] = first;
+        L.prefix[c] = pre;
+        first += L.count[c];
+        pre += L.count[c] + 1;
     }
-    P.off_start = align256(sizeof(BatchImage) * (size_t)n);
-    P.ws_bytes = P.off_start + sizeof(int64_t) * (size_t)(n + 1);
+    int fill[kClasses];
+    for (int c = 0; c < kClasses; ++c) {
+        fill[c] = 0;
+        start_out[L.prefix[c]] = 0;
+    }
+    for (int k = 0; k < n; ++k) {   // stable: images keep their order within a class
+        const int c = tmp_cls[k];
+        const int pos = fill[c]++;
+        imgs_out[L.first[c] + pos] = tmp_imgs[k];
+        int64_t* st = start_out + L.prefix[c];
+        st[pos + 1] = st[pos] + tmp_items[k];
+    }
+    for (int c = 0; c < kClasses; ++c) L.total[c] = start_out[L.prefix[c] + L.count[c]];
     return RS_OK;
 }
 
-template <typename T>
-static void* batched_func() { return reinterpret_cast<void*>(&k_batched<T>); }
+template <int KT, int C, typename T>
+static void* win_func() { return reinterpret_cast<void*>(&k_batched_window<KT, C, T>); }
 
-static void* batched_kernel(int dtype)
+template <typename T>
+static void* class_func_t(int c)
 {
-    switch (dtype) {
-    case DT_U8: return batched_func<uint8_t>();
-    case DT_F16: return batched_func<__half>();
-    case DT_BF16: return batched_func<__nv_bfloat16>();
-    default: return batched_func<float>();
+    switch (c) {
+    case 0: return win_func<2, 1, T>();
+    case 1: return win_func<2, 2, T>();
+    case 2: return win_func<2, 3, T>();
+    case 3: return win_func<2, 4, T>();
+    case 4: return win_func<4, 1, T>();
+    case 5: return win_func<4, 2, T>();
+    case 6: return win_func<4, 3, T>();
+    case 7: return win_func<4, 4, T>();
+    default: return reinterpret_cast<void*>(&k_batched<T>);
     }
 }
 
-struct BatchLaunch {
+static void* class_func(int dtype, int c)
+{
+    switch (dtype) {
+    case DT_U8: return class_func_t<uint8_t>(c);
+    case DT_F16: return class_func_t<__half>(c);
+    case DT_BF16: return class_func_t<__nv_bfloat16>(c);
+    default: return class_func_t<float>(c);
+    }
+}
+
+// Launch parameters of one class (kernel arguments live in the struct so a
+// graph node can point at them while it is created).
+struct ClassLaunch {
     void* func;
     dim3 grid, block;
     size_t smem;
@@ -205,29 +331,68 @@ struct BatchLaunch {
     unsigned int* fault;
 };
 
-static cudaError_t batch_launch_params(const BatchPlanHost& P, int dtype, const rs_options& o, void* ws,
-                                       BatchLaunch& L)
+static cudaError_t class_launches(const BatchLayout& L, int dtype, const rs_options& o, const void* imgs_dev,
+                                  const void* start_dev, ClassLaunch* out, int& nl)
 {
-    L.func = batched_kernel(dtype);
-    cudaError_t e = cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.func, P.threads, P.smem);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, per_sm);
-    const int64_t total = P.start.back();
-    const int64_t blocks = std::min<int64_t>(total, (int64_t)num_sms() * per_sm);
-    L.grid = dim3((unsigned)std::max<int64_t>(1, blocks));
-    L.block = dim3(P.threads);
-    L.smem = P.smem;
-    L.imgs = static_cast<const BatchImage*>(ws);
-    L.start = reinterpret_cast<const int64_t*>(static_cast<char*>(ws) + P.off_start);
-    L.n = (int)P.imgs.size();
-    L.total = total;
-    L.coord = o.coord;
-    L.a = o.cubic_a;
-    L.fault = fault_word();
+    nl = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        if (L.count[c] == 0 || L.total[c] == 0) continue;
+        ClassLaunch& cl = out[nl++];
+        cl.func = class_func(dtype, c);
+        const int threads = c == kTileClass ? L.threads : 256;
+        cudaError_t e = cudaFuncSetAttribute(cl.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem[c]);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cl.func, threads, L.smem[c]);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::min<int64_t>(L.total[c], (int64_t)num_sms() * std::max(1, per_sm));
+        cl.grid = dim3((unsigned)std::max<int64_t>(1, blocks));
+        cl.block = dim3(threads);
+        cl.smem = L.smem[c];
+        cl.imgs = static_cast<const BatchImage*>(imgs_dev) + L.first[c];
+        cl.start = static_cast<const int64_t*>(start_dev) + L.prefix[c];
+        cl.n = L.count[c];
+        cl.total = L.total[c];
+        cl.coord = o.coord;
+        cl.a = o.cubic_a;
+        cl.fault = fault_word();
+    }
     return cudaSuccess;
+}
+
+static cudaError_t launch_classes(ClassLaunch* cls, int nl, cudaStream_t st)
+{
+    for (int i = 0; i < nl; ++i) {
+        ClassLaunch& c = cls[i];
+        void* args[] = {&c.imgs, &c.start, &c.n, &c.total, &c.coord, &c.a, &c.fault};
+        cudaError_t e = cudaLaunchKernel(c.func, c.grid, c.block, args, c.smem, st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Host-side work list for the workspace entry points.
+struct BatchPlanHost {
+    std::vector<BatchImage> imgs;
+    std::vector<int64_t> start;
+    BatchLayout L;
+    size_t ws_bytes = 0, off_start = 0;
+};
+
+static rs_status batch_prepare(const rs_image_desc* d, int n, int dtype, const rs_options& o, BatchPlanHost& P)
+{
+    if (!d || n < 1 || n > (1 << 20)) return RS_ERR_INVALID_ARG;
+    P.imgs.resize(n);
+    P.start.assign((size_t)n + kClasses, 0);
+    std::vector<BatchImage> tmp(n);
+    std::vector<int> cls(n);
+    std::vector<int64_t> items(n);
+    rs_status s = batch_layout(d, n, dtype, o, P.imgs.data(), P.start.data(), tmp.data(), cls.data(), items.data(), P.L);
+    if (s != RS_OK) return s;
+    P.off_start = align256(sizeof(BatchImage) * (size_t)n);
+    P.ws_bytes = P.off_start + sizeof(int64_t) * P.start.size();
+    return RS_OK;
 }
 
 static cudaError_t upload(const BatchPlanHost& P, void* ws, cudaStream_t st)
@@ -239,13 +404,6 @@ static cudaError_t upload(const BatchPlanHost& P, void* ws, cudaStream_t st)
     if (e != cudaSuccess) return e;
     // The host blob dies with this function: wait for the copy to finish.
     return cudaStreamSynchronize(st);
-}
-
-static cudaError_t launch_now(BatchLaunch& L, cudaStream_t st)
-{
-    void* args[] = {&L.imgs, &L.start, &L.n, &L.total, &L.coord, &L.a, &L.fault};
-    cudaError_t e = cudaLaunchKernel(L.func, L.grid, L.block, args, L.smem, st);
-    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 static rs_status check_ws(const BatchPlanHost& P, void* ws, size_t bytes)
@@ -273,67 +431,17 @@ static rs_status check_ws(const BatchPlanHost& P, void* ws, size_t bytes)
 // device current) and passed to the kernel like any other pointer.
 static constexpr int kNoAllocMaxImages = 4096;
 static constexpr size_t kNoAllocImgBytes = ((sizeof(BatchImage) * kNoAllocMaxImages + 255) / 256) * 256;
-static constexpr size_t kNoAllocBytes = kNoAllocImgBytes + sizeof(int64_t) * (kNoAllocMaxImages + 1);
+static constexpr size_t kNoAllocBytes = kNoAllocImgBytes + sizeof(int64_t) * (kNoAllocMaxImages + kClasses);
 static __device__ __align__(256) unsigned char g_batch_scratch[kNoAllocBytes];
 
 static constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;                               // guards everything below
 static void* g_noalloc_dev[kNoAllocMaxDevices];               // device address per device
 static BatchImage g_noalloc_imgs[kNoAllocMaxImages];           // host staging (no heap use)
-static int64_t g_noalloc_start[kNoAllocMaxImages + 1];
-
-// Same validation and tiling as batch_prepare, written into the fixed
-// host staging arrays instead of vectors.
-static rs_status noalloc_prepare(const rs_image_desc* d, int n, int dtype, const rs_options& o, size_t& smem,
-                                 int& threads)
-{
-    if (!d || n < 1) return RS_ERR_INVALID_ARG;
-    if (n > kNoAllocMaxImages) return RS_ERR_WORKSPACE;
-    if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
-    rs_status s = check_options(o, RS_BILINEAR);
-    if (s != RS_OK) return s;
-    const int tile_w = o.tile_w ? o.tile_w : 512;
-    const int h_cap = o.tile_h ? o.tile_h : 32;
-    threads = o.threads ? o.threads : 256;
-    if (threads != 128 && threads != 256) return RS_ERR_INVALID_ARG;
-    const int64_t es = (int64_t)dtype_size(dtype);
-    auto src_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.H - 1) * x.src_pitch + (int64_t)x.W * x.C) * es; };
-    auto dst_bytes = [&](const rs_image_desc& x) { return ((int64_t)(x.Ho - 1) * x.dst_pitch + (int64_t)x.Wo * x.C) * es; };
-    g_noalloc_start[0] = 0;
-    smem = 0;
-    for (int k = 0; k < n; ++k) {
-        const rs_image_desc& x = d[k];
-        if (!x.src || !x.dst) return RS_ERR_INVALID_ARG;
-        if (!dim_ok(x.H) || !dim_ok(x.W) || !dim_ok(x.Ho) || !dim_ok(x.Wo)) return RS_ERR_INVALID_ARG;
-        if (x.C < 1 || x.C > 4) return RS_ERR_INVALID_ARG;
-        if (x.method < RS_NEAREST || x.method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
-        if (x.src_pitch < (int64_t)x.W * x.C || x.dst_pitch < (int64_t)x.Wo * x.C) return RS_ERR_INVALID_ARG;
-        if (reinterpret_cast<uintptr_t>(x.src) % es || reinterpret_cast<uintptr_t>(x.dst) % es)
-            return RS_ERR_ALIGNMENT;
-        Geom g;
-        g.H = x.H; g.W = x.W; g.Ho = x.Ho; g.Wo = x.Wo; g.C = x.C;
-        g.src_pitch = x.src_pitch; g.dst_pitch = x.dst_pitch;
-        g.sp = PlaneMap{0, 0, 1}; g.dp = PlaneMap{0, 0, 1};
-        g.planes = 1; g.coord = o.coord; g.a = o.cubic_a;
-        TileCfg c;
-        if (!image_tile(g, x.method, tile_w, h_cap, threads, 72 * 1024, c)) return RS_ERR_UNSUPPORTED;
-        BatchImage& im = g_noalloc_imgs[k];
-        std::memset(&im, 0, sizeof im);
-        im.src = x.src; im.dst = x.dst;
-        im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
-        im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
-        im.tile_w = c.tile_w; im.tile_h = c.tile_h; im.sh_max = c.sh_max; im.swe_max = c.swe_max;
-        im.tiles_x = (int)(((int64_t)x.Wo * x.C + c.tile_w - 1) / c.tile_w);
-        g_noalloc_start[k + 1] = g_noalloc_start[k] + (int64_t)im.tiles_x * ((x.Ho + c.tile_h - 1) / c.tile_h);
-        smem = std::max(smem, c.smem);
-    }
-    for (int k = 0; k < n; ++k)
-        for (int l = 0; l < n; ++l) {
-            if (overlaps(d[k].dst, dst_bytes(d[k]), d[l].src, src_bytes(d[l]))) return RS_ERR_INVALID_ARG;
-            if (l != k && overlaps(d[k].dst, dst_bytes(d[k]), d[l].dst, dst_bytes(d[l]))) return RS_ERR_INVALID_ARG;
-        }
-    return RS_OK;
-}
+static int64_t g_noalloc_start[kNoAllocMaxImages + kClasses];
+static BatchImage g_noalloc_tmp[kNoAllocMaxImages];
+static int g_noalloc_cls[kNoAllocMaxImages];
+static int64_t g_noalloc_items[kNoAllocMaxImages];
 
 }  // namespace rs
 
@@ -342,10 +450,12 @@ extern "C" rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs
 {
     using namespace rs;
     const rs_options o = options_or_default(opt);
+    if (!d || n < 1) return RS_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxImages) return RS_ERR_WORKSPACE;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    size_t smem = 0;
-    int threads = 256;
-    rs_status s = noalloc_prepare(d, n, dtype, o, smem, threads);
+    BatchLayout L;
+    rs_status s = batch_layout(d, n, dtype, o, g_noalloc_imgs, g_noalloc_start, g_noalloc_tmp, g_noalloc_cls,
+                               g_noalloc_items, L);
     if (s != RS_OK) return s;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -363,27 +473,14 @@ extern "C" rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs
     // so the staging arrays may be refilled by the next call.
     e = cudaMemcpyAsync(scratch, g_noalloc_imgs, sizeof(BatchImage) * (size_t)n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(scratch + kNoAllocImgBytes, g_noalloc_start, sizeof(int64_t) * (size_t)(n + 1),
+        e = cudaMemcpyAsync(scratch + kNoAllocImgBytes, g_noalloc_start, sizeof(int64_t) * (size_t)(n + kClasses),
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
-    void* func = batched_kernel(dtype);
-    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    ClassLaunch cls[kClasses];
+    int nl = 0;
+    if ((e = class_launches(L, dtype, o, scratch, scratch + kNoAllocImgBytes, cls, nl)) != cudaSuccess)
         return cuda_status(e);
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem)) != cudaSuccess)
-        return cuda_status(e);
-    const int64_t total = g_noalloc_start[n];
-    const int64_t blocks = std::min<int64_t>(total, (int64_t)num_sms() * std::max(1, per_sm));
-    const BatchImage* imgs = reinterpret_cast<const BatchImage*>(scratch);
-    const int64_t* start = reinterpret_cast<const int64_t*>(scratch + kNoAllocImgBytes);
-    int nn = n, coord = o.coord;
-    float a = o.cubic_a;
-    int64_t tot = total;
-    unsigned int* fw = fault_word();
-    void* args[] = {&imgs, &start, &nn, &tot, &coord, &a, &fw};
-    e = cudaLaunchKernel(func, dim3((unsigned)std::max<int64_t>(1, blocks)), dim3(threads), args, smem, st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    return cuda_status(e);
+    return cuda_status(launch_classes(cls, nl, st));
 }
 
 using namespace rs;
@@ -419,9 +516,12 @@ rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype, void*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(P, workspace, st);
     if (e != cudaSuccess) return cuda_status(e);
-    BatchLaunch L;
-    if ((e = batch_launch_params(P, dtype, o, workspace, L)) != cudaSuccess) return cuda_status(e);
-    return cuda_status(launch_now(L, st));
+    ClassLaunch cls[kClasses];
+    int nl = 0;
+    if ((e = class_launches(P.L, dtype, o, workspace, static_cast<char*>(workspace) + P.off_start, cls, nl)) !=
+        cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(launch_classes(cls, nl, st));
 }
 
 rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype, void* workspace,
@@ -437,23 +537,31 @@ rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(P, workspace, st);
     if (e != cudaSuccess) return cuda_status(e);
-    BatchLaunch L;
-    if ((e = batch_launch_params(P, dtype, o, workspace, L)) != cudaSuccess) return cuda_status(e);
+    ClassLaunch cls[kClasses];
+    int nl = 0;
+    if ((e = class_launches(P.L, dtype, o, workspace, static_cast<char*>(workspace) + P.off_start, cls, nl)) !=
+        cudaSuccess)
+        return cuda_status(e);
 
     rs_batched_plan* p = new rs_batched_plan();
     cudaGetDevice(&p->device);
-    void* args[] = {&L.imgs, &L.start, &L.n, &L.total, &L.coord, &L.a, &L.fault};
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof kp);
-    kp.func = L.func;
-    kp.gridDim = L.grid;
-    kp.blockDim = L.block;
-    kp.sharedMemBytes = (unsigned)L.smem;
-    kp.kernelParams = args;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphCreate(&p->graph, 0)) == cudaSuccess &&
-        (e = cudaGraphAddKernelNode(&node, p->graph, nullptr, 0, &kp)) == cudaSuccess)
-        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    e = cudaGraphCreate(&p->graph, 0);
+    // One kernel node per class, with no dependencies between them: the
+    // class launches may run concurrently.
+    for (int i = 0; i < nl && e == cudaSuccess; ++i) {
+        ClassLaunch& c = cls[i];
+        void* args[] = {&c.imgs, &c.start, &c.n, &c.total, &c.coord, &c.a, &c.fault};
+        cudaKernelNodeParams kp;
+        std::memset(&kp, 0, sizeof kp);
+        kp.func = c.func;
+        kp.gridDim = c.grid;
+        kp.blockDim = c.block;
+        kp.sharedMemBytes = (unsigned)c.smem;
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, p->graph, nullptr, 0, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
     if (e != cudaSuccess) {
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);

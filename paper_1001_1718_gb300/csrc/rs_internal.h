@@ -72,7 +72,7 @@ struct StreamCfg {
 // and `waves`), source rows staged in chunks of `chunk` rows (double
 // buffered) of swe_max elements; vec = 16-byte loads.
 struct PolyCfg {
-    int chunk, band_h, waves, swe_max, band_cap, vec;
+    int chunk, band_h, waves, swe_max, band_cap, pos_cap, vec;
     size_t smem;
 };
 
