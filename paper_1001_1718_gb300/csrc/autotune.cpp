@@ -113,9 +113,15 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
         const Tuned t{RS_IMPL_GATHER, 64 * (16 / (int)dtype_size(dtype)), 16, 256, 0};
         if (make_choice(g, method, dtype, src, t, k)) return true;
     }
-    for (int ch : {8, 4}) {   // register window, 8-row chunks within ~100 KB
-        const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
-        if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= 100 * 1024) return true;
+    // Register window for vertical upscales of large outputs (at a
+    // downscale a chunk covers few output rows; a small output has too few
+    // strips and bands to fill the GPU), 8-row chunks within ~100 KB.
+    const int64_t out_elems = (int64_t)g.Ho * g.Wo * g.C * g.planes;
+    if (g.Ho >= g.H && out_elems >= (int64_t)1 << 22) {
+        for (int ch : {8, 4}) {
+            const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
+            if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= 100 * 1024) return true;
+        }
     }
     StreamCfg sc = stream_default(g, method, dtype, src);
     if (sc.tile_w) {

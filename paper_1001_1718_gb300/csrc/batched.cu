@@ -36,7 +36,7 @@ struct BatchImage {
     int H, W, Ho, Wo;
     int C, method, tiles_x, kind;          // tiles_x: items per row of items; kind 0 tile, 1 window
     int tile_w, tile_h, sh_max, swe_max;   // kind 0: tiled-kernel tile
-    int chunk, band_h, w_swe_max, band_cap, pos_cap, vec, pad0, pad1;   // kind 1: window config
+    int chunk, band_h, w_swe_max, band_cap, pos_cap, vec, raw_row, raw_off;   // kind 1: window config
 };
 
 // Classes: 0..7 = window (KT 2 / 4) x (C 1..4), 8 = tiled.
@@ -91,6 +91,8 @@ k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict_
         pc.band_cap = im.band_cap;
         pc.pos_cap = im.pos_cap;
         pc.vec = im.vec;
+        pc.raw_row = im.raw_row;
+        pc.raw_off = im.raw_off;
         pc.smem = 0;
         poly_body<KT, C, T>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), pc,
                             (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
@@ -202,6 +204,8 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
             im.band_cap = pc.band_cap;
             im.pos_cap = pc.pos_cap;
             im.vec = pc.vec;
+            im.raw_row = pc.raw_row;
+            im.raw_off = pc.raw_off;
             im.tiles_x = (int)(((int64_t)x.Wo * x.C + 1023) / 1024);
             items = (int64_t)im.tiles_x * ((x.Ho + im.band_h - 1) / im.band_h);
             smem = pc.smem;

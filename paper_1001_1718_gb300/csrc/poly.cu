@@ -43,8 +43,11 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
     c.swe_max = ((span_px * g.C + 2 * EPU + 4) + 3) & ~3;
     c.band_cap = std::min(kPolyMaxBand, g.Ho);
     c.pos_cap = poly_span_bound(c.band_cap, g.H, g.Ho, KT);   // source positions of a band
-    c.smem = sizeof(float) * (2 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KT) +
-             sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);
+    const size_t tables = sizeof(float) * (2 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KT) +
+                          sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);
+    c.raw_off = (int)((tables + 15) & ~(size_t)15);
+    c.raw_row = c.vec ? (c.swe_max / EPU + 2) * 16 : 0;
+    c.smem = (size_t)c.raw_off + 3 * (size_t)c.chunk * c.raw_row;
     return c.smem <= max_smem_per_block();
 }
 

@@ -13,10 +13,12 @@
 //   - every output row i with f(i) == b is blended from the window (packed
 //     FP32x2 FMAs), rounded and stored.
 // The position loop is unrolled KT times so the window rotates by register
-// renaming. Source rows are staged in chunks of R rows; the raw 16-byte
-// loads of chunk c + 1 are issued before chunk c is processed and converted
-// into the other half of a double buffer afterwards, so one barrier per
-// chunk suffices. Out-of-image rows and columns take the edge pixel.
+// renaming. Source rows are staged in chunks of R rows as FP32 (double
+// buffered). With 16-byte-aligned rows the raw bytes of chunks c + 1 and
+// c + 2 are already on their way (cp.async into a three-slot raw ring) while
+// chunk c is processed; each thread converts the units it copied itself, so
+// one barrier per chunk suffices. Out-of-image rows and columns take the
+// edge pixel.
 #pragma once
 
 #include <algorithm>
@@ -159,6 +161,12 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     float* RW = SR + 2 * R * cfg.swe_max;                  // [band_cap][KT]
     int* RF = reinterpret_cast<int*>(RW + cfg.band_cap * KT);   // [band_cap] first taps
     int* NC = RF + cfg.band_cap;                           // [pos_cap] rows per position
+    // Raw 16-byte load units of the next two chunks (vector path): [3][R][raw_row].
+    unsigned char* RAW = reinterpret_cast<unsigned char*>(sm) + cfg.raw_off;
+    if (cfg.vec && units * 16 > cfg.raw_row) {   // uniform; the host sizes raw rows
+        if (tid == 0) report_fault(fault, FAULT_TILE_SRC_SPAN);
+        return;
+    }
 
     // Row taps of the band.
     for (int i = tid; i < nrows; i += kPolyThreads) {
@@ -213,75 +221,51 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
             dstb[k * cfg.swe_max + pos] = Store<T>::load(row_ptr(r0 + k) + src_el);
         }
     };
-    constexpr int kPolyPrefetch = sizeof(T) == 1 ? 2 : 4;
-    uint4 pf[kPolyPrefetch];
-    const int pf_cap = kPolyPrefetch * kPolyThreads;
-    auto issue = [&](int r0, int nn) {
-        #pragma unroll
-        for (int i = 0; i < kPolyPrefetch; ++i) {
-            const int u = tid + i * kPolyThreads;
-            if (u < nn * units) {
-                int k, w;
-                split(u, k, w);
-                pf[i] = __ldg(reinterpret_cast<const uint4*>(row_ptr(r0 + k) + a0 + w * EPU));
-            }
+    // Vector path: cp.async copies of 16-byte units into raw slot `slot`,
+    // one commit group per chunk. Each thread later converts exactly the
+    // units it copied, so its own wait_group makes them visible to it.
+    auto issue_async = [&](int r0, int nn, int slot) {
+        unsigned char* rb = RAW + (size_t)slot * R * cfg.raw_row;
+        for (int u = tid; u < nn * units; u += kPolyThreads) {
+            int k, w;
+            split(u, k, w);
+            const T* gsrc = row_ptr(r0 + k) + a0 + w * EPU;
+            const unsigned sdst = (unsigned)__cvta_generic_to_shared(rb + k * cfg.raw_row + w * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(gsrc) : "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto commit = [&](int r0, int nn, float* dstb) {
-        #pragma unroll
-        for (int i = 0; i < kPolyPrefetch; ++i) {
-            const int u = tid + i * kPolyThreads;
-            if (u < nn * units) {
-                int k, w;
-                split(u, k, w);
-                poly_unpack16<T>(pf[i], dstb + k * cfg.swe_max + u0 + w * EPU);
-            }
+    auto convert = [&](int r0, int nn, int slot, float* dstb) {
+        const unsigned char* rb = RAW + (size_t)slot * R * cfg.raw_row;
+        for (int u = tid; u < nn * units; u += kPolyThreads) {
+            int k, w;
+            split(u, k, w);
+            const uint4 v = *reinterpret_cast<const uint4*>(rb + k * cfg.raw_row + w * 16);
+            poly_unpack16<T>(v, dstb + k * cfg.swe_max + u0 + w * EPU);
         }
         if (lpad + rpad) pads(r0, nn, dstb);
     };
+    // Element path (rows not 16-byte aligned): synchronous staging.
     auto stage_sync = [&](int r0, int nn, float* dstb) {
         const int total = nn * units;
-        if (cfg.vec) {
-            for (int b0 = 0; b0 < total; b0 += pf_cap) {
-                #pragma unroll
-                for (int i = 0; i < kPolyPrefetch; ++i) {
-                    const int u = b0 + tid + i * kPolyThreads;
-                    if (u < total) {
-                        int k, w;
-                        split(u, k, w);
-                        pf[i] = __ldg(reinterpret_cast<const uint4*>(row_ptr(r0 + k) + a0 + w * EPU));
-                    }
-                }
-                #pragma unroll
-                for (int i = 0; i < kPolyPrefetch; ++i) {
-                    const int u = b0 + tid + i * kPolyThreads;
-                    if (u < total) {
-                        int k, w;
-                        split(u, k, w);
-                        poly_unpack16<T>(pf[i], dstb + k * cfg.swe_max + u0 + w * EPU);
-                    }
+        for (int b0 = 0; b0 < total; b0 += 4 * kPolyThreads) {
+            float v[4];
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int u = b0 + tid + i * kPolyThreads;
+                if (u < total) {
+                    int k, w;
+                    split(u, k, w);
+                    v[i] = Store<T>::load(row_ptr(r0 + k) + a0 + w);
                 }
             }
-        } else {
-            for (int b0 = 0; b0 < total; b0 += 4 * kPolyThreads) {
-                float v[4];
-                #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int u = b0 + tid + i * kPolyThreads;
-                    if (u < total) {
-                        int k, w;
-                        split(u, k, w);
-                        v[i] = Store<T>::load(row_ptr(r0 + k) + a0 + w);
-                    }
-                }
-                #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int u = b0 + tid + i * kPolyThreads;
-                    if (u < total) {
-                        int k, w;
-                        split(u, k, w);
-                        dstb[k * cfg.swe_max + u0 + w] = v[i];
-                    }
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int u = b0 + tid + i * kPolyThreads;
+                if (u < total) {
+                    int k, w;
+                    split(u, k, w);
+                    dstb[k * cfg.swe_max + u0 + w] = v[i];
                 }
             }
         }
@@ -317,14 +301,20 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     }
     // Source rows in order: b_first .. b_last + KT - 1, in chunks of R.
     const int r_first = b_first, r_end = b_last + KT;      // [r_first, r_end)
+    auto chunk_rows = [&](int c) { return max(0, min(R, r_end - (r_first + c * R))); };
+    int cidx = 0;                                          // current chunk
     int chunk_lo = r_first;
-    int nn = min(R, r_end - chunk_lo);
-    stage_sync(chunk_lo, nn, SR);
-    int next_lo = chunk_lo + nn;
-    int next_nn = min(R, r_end - next_lo);
-    bool pref = cfg.vec && next_nn > 0 && next_nn * units <= pf_cap;
+    int nn = chunk_rows(0);
+    if (cfg.vec) {
+        issue_async(r_first, nn, 0);
+        issue_async(r_first + R, chunk_rows(1), 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        convert(r_first, nn, 0, SR);
+    } else {
+        stage_sync(r_first, nn, SR);
+    }
     __syncthreads();
-    if (pref) issue(next_lo, next_nn);
+    if (cfg.vec) issue_async(r_first + 2 * R, chunk_rows(2), 2);
     int half = 0;
 
     // Register window: h[p] holds source row (b + p) at position b.
@@ -384,21 +374,26 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
             if (b <= b_last) {
                 // Make source row r = b + KT - 1 available in the staged chunk.
                 if (r >= chunk_lo + nn) {
-                    // Move to the next chunk. The other half held chunk k-1,
+                    // Move to chunk c = cidx + 1. Its FP32 half held chunk c-2,
                     // whose reads all precede the barrier of the previous
-                    // switch, so it can be overwritten now; the barrier below
-                    // publishes the new chunk.
+                    // switch; its raw slot was filled two switches ago (wait
+                    // for this thread's copies, at most one newer group may
+                    // still be in flight). The barrier publishes the chunk;
+                    // then chunk c+2 is issued into the raw slot of chunk c-1,
+                    // which this thread has already converted.
+                    ++cidx;
                     half ^= 1;
+                    chunk_lo = r_first + cidx * R;
+                    nn = chunk_rows(cidx);
                     float* dstb = SR + half * R * cfg.swe_max;
-                    if (pref) commit(next_lo, next_nn, dstb);
-                    else stage_sync(next_lo, next_nn, dstb);
-                    chunk_lo = next_lo;
-                    nn = next_nn;
-                    next_lo = chunk_lo + nn;
-                    next_nn = min(R, r_end - next_lo);
-                    pref = cfg.vec && next_nn > 0 && next_nn * units <= pf_cap;
+                    if (cfg.vec) {
+                        asm volatile("cp.async.wait_group 1;" ::: "memory");
+                        convert(chunk_lo, nn, cidx % 3, dstb);
+                    } else {
+                        stage_sync(chunk_lo, nn, dstb);
+                    }
                     __syncthreads();
-                    if (pref) issue(next_lo, next_nn);
+                    if (cfg.vec) issue_async(r_first + (cidx + 2) * R, chunk_rows(cidx + 2), (cidx + 2) % 3);
                 }
                 // the newest row goes into slot (u + KT - 1) % KT
                 const int ns = (u + KT - 1) % KT;

@@ -73,6 +73,7 @@ struct StreamCfg {
 // buffered) of swe_max elements; vec = 16-byte loads.
 struct PolyCfg {
     int chunk, band_h, waves, swe_max, band_cap, pos_cap, vec;
+    int raw_row, raw_off;   // vector path: bytes per raw staged row, byte offset of the raw ring
     size_t smem;
 };
 
