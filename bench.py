@@ -156,10 +156,21 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # GPU arm
 
-def kernel_source_sha() -> str:
+# Source files each profiled kernel is built from (a change to any of them
+# voids its recorded DRAM traffic).
+KERNEL_SOURCES = {
+    "k_poly": ["poly.cu", "poly_body.cuh", "rs_common.cuh", "rs_internal.h"],
+    "k_stream": ["stream.cu", "rs_common.cuh", "rs_internal.h"],
+    "k_tiled": ["tiled.cu", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
+    "k_nearest": ["nearest.cu", "rs_common.cuh", "rs_internal.h"],
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_1001_1718_gb300" / "csrc").glob("*")):
-        h.update(p.read_bytes())
+    csrc = ROOT / "paper_1001_1718_gb300" / "csrc"
+    for name in KERNEL_SOURCES.get(kernel, sorted(p.name for p in csrc.glob("*"))):
+        h.update((csrc / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -174,7 +185,7 @@ def traffic_from_profile(kernel: str, workload: str):
         if ":" in line:
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_sha") != kernel_source_sha():
+    if kv.get("source_sha") != kernel_source_sha(kernel):
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
