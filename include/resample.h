@@ -158,9 +158,11 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
  * gather form: every input sample sums, in a fixed order, the output
  * samples whose taps name it, so results are deterministic (no atomics).
  * grad_in is OVERWRITTEN. `workspace` is a device buffer of at least the
- * size rs_resize_backward_workspace() reports (per-axis transposed weight
- * tables); it is written by the call and may be reused after the call's
- * work on `stream` has finished.
+ * size rs_resize_backward_workspace() reports: the per-axis transposed weight
+ * tables and an FP32 intermediate (the x-transposed rows of a group of
+ * planes, at most ~64 MB); it is written by the call and may be reused after
+ * the call's work on `stream` has finished. opt->impl = RS_IMPL_TILED selects
+ * the single-pass tiled kernel instead (tables only are used).
  */
 rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in,
                                        rs_method method, const rs_options* opt,

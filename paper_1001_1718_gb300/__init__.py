@@ -152,15 +152,16 @@ def backward_workspace_bytes(grad_out: torch.Tensor, in_hw, method, *, layout="n
 
 def resize_backward(grad_out: torch.Tensor, in_hw, method="bilinear", *, layout: str = "nchw",
                     coord="asymmetric", cubic_a: float = -0.5, grad_in: torch.Tensor | None = None,
-                    workspace: torch.Tensor | None = None) -> torch.Tensor:
-    """Adjoint of resize() for FP32: grad_in = A^T grad_out (deterministic)."""
+                    workspace: torch.Tensor | None = None, impl="auto") -> torch.Tensor:
+    """Adjoint of resize() for FP32: grad_in = A^T grad_out (deterministic).
+    impl="auto" runs the two-pass kernels, impl="tiled" the single-pass one."""
     _require_cuda(grad_out)
     H, W = int(in_hw[0]), int(in_hw[1])
     if grad_in is None:
         grad_in = torch.empty(_out_shape(grad_out, layout, H, W), dtype=grad_out.dtype,
                               device=grad_out.device)
     Lo, Li = _layout(grad_out, layout), _layout(grad_in, layout)
-    o = _opts(coord, cubic_a, "auto", None, 0)
+    o = _opts(coord, cubic_a, impl, None, 0)
     m = _code(METHODS, method, "method")
     n = ctypes.c_size_t(0)
     B.check(lib().rs_resize_backward_workspace(ctypes.byref(Lo), ctypes.byref(Li), m, ctypes.byref(o),

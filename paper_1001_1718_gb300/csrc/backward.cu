@@ -10,10 +10,16 @@
 // 1. k_adjoint_table builds, per axis, jlo(i), the range length and the
 //    summed weights w(i, j) = sum over taps q of output j with
 //    clamp(first(j) + q) == i, into the caller's workspace.
-// 2. k_adjoint computes a tile of dX: it stages the dY footprint of the tile
-//    in shared memory, applies the x-axis transpose to every staged row, then
-//    the y-axis transpose, and writes dX. Every dX element is one fixed-order
-//    sum, so the result is deterministic (no atomics).
+// 2. Default: two memory-bound passes per group of planes through an FP32
+//    intermediate T in the workspace: k_adj_x applies the x-axis transpose to
+//    every dY row (T = dY Ax, Ho x W), k_adj_y the y-axis transpose
+//    (dX = Ay^T T). Both are coalesced along rows; each thread keeps its
+//    column's (or row's) transposed weights in registers and walks several
+//    rows. Alternatively (RS_IMPL_TILED) k_adjoint computes a tile of dX in
+//    one pass: it stages the dY footprint of the tile in shared memory,
+//    applies the x-axis transpose to every staged row, then the y-axis
+//    transpose. Every dX element is one fixed-order sum, so the result is
+//    deterministic (no atomics).
 #include <algorithm>
 #include <vector>
 
@@ -233,6 +239,63 @@ k_adjoint(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, co
 }
 
 // ---------------------------------------------------------------------------
+// Two-pass adjoint.
+
+static constexpr int kAdjThreads = 256;
+
+// T[p][j][e] = sum_k wx[x][k] dY[p][j][(xlo(x) + k) C + c] for the dY rows
+// j of this block (e = x C + c). T has rows of W C elements.
+template <int KXM>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adj_x(const Geom g, const float* __restrict__ dY, float* __restrict__ T, const AdjTables tb, int plane0,
+        int rows_per_thread)
+{
+    const int64_t WC = (int64_t)g.W * g.C;
+    const int64_t e = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    if (e >= WC) return;
+    const int pl = blockIdx.z;
+    const int x = (int)(e / g.C), c = (int)(e - (int64_t)x * g.C);
+    const int lo = __ldg(tb.xlo + x);
+    const int cnt = min(__ldg(tb.xcnt + x), KXM);
+    float w[KXM];
+    #pragma unroll
+    for (int k = 0; k < KXM; ++k) w[k] = k < cnt ? __ldg(tb.xw + (int64_t)x * tb.xK + k) : 0.0f;
+    const float* src = dY + g.dp.offset(plane0 + pl) + (int64_t)lo * g.C + c;
+    float* dst = T + (int64_t)pl * g.Ho * WC + e;
+    const int j0 = blockIdx.y * rows_per_thread, j1 = min(g.Ho, j0 + rows_per_thread);
+    for (int j = j0; j < j1; ++j) {
+        const float* row = src + (int64_t)j * g.dst_pitch;
+        float acc = 0.0f;
+        #pragma unroll
+        for (int k = 0; k < KXM; ++k)
+            if (k < cnt) acc = fmaf(w[k], __ldg(row + (int64_t)k * g.C), acc);
+        dst[(int64_t)j * WC] = acc;
+    }
+}
+
+// dX[p][i][e] = sum_a wy[i][a] T[p][ylo(i) + a][e] for the dX rows i of
+// this block.
+__global__ void __launch_bounds__(kAdjThreads)
+k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const AdjTables tb, int plane0,
+        int rows_per_thread)
+{
+    const int64_t WC = (int64_t)g.W * g.C;
+    const int64_t e = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    if (e >= WC) return;
+    const int pl = blockIdx.z;
+    const float* src = T + (int64_t)pl * g.Ho * WC + e;
+    float* dst = dX + g.sp.offset(plane0 + pl) + e;
+    const int i0 = blockIdx.y * rows_per_thread, i1 = min(g.H, i0 + rows_per_thread);
+    for (int i = i0; i < i1; ++i) {
+        const int lo = __ldg(tb.ylo + i), cnt = __ldg(tb.ycnt + i);
+        const float* wr = tb.yw + (int64_t)i * tb.yK;
+        float acc = 0.0f;
+        for (int a = 0; a < cnt; ++a) acc = fmaf(__ldg(wr + a), __ldg(src + (int64_t)(lo + a) * WC), acc);
+        dst[(int64_t)i * g.src_pitch] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -241,7 +304,11 @@ struct BwdPlan {
     int yK, xK;
     size_t ws_bytes;
     size_t off_ylo, off_ycnt, off_yw, off_xlo, off_xcnt, off_xw;
+    size_t off_t;        // two-pass intermediate T (group_planes x Ho x W C floats)
+    int group_planes;
 };
+
+static constexpr size_t kAdjTBudget = (size_t)64 << 20;   // bytes of T per plane group
 
 static BwdPlan plan_tables(const Geom& g, int method)
 {
@@ -257,6 +324,9 @@ static BwdPlan plan_tables(const Geom& g, int method)
     p.off_xlo = o; o = align256(o + sizeof(int) * g.W);
     p.off_xcnt = o; o = align256(o + sizeof(int) * g.W);
     p.off_xw = o; o = align256(o + sizeof(float) * (size_t)g.W * p.xK);
+    const size_t plane_t = sizeof(float) * (size_t)g.Ho * g.W * g.C;
+    p.group_planes = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.planes, kAdjTBudget / plane_t));
+    p.off_t = o; o = align256(o + plane_t * p.group_planes);
     p.ws_bytes = o;
     return p;
 }
@@ -368,10 +438,16 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     }
     const int KX = p.xK;
     if (KX > 64) return RS_ERR_UNSUPPORTED;   // > 16x upscale along x
+    // Two passes for upscales (dY larger than dX); the single-pass tiled
+    // kernel for downscales, where it measures faster.
+    const bool two_pass = o.impl != RS_IMPL_TILED && KX <= 32 &&
+                          (int64_t)g.Ho * g.Wo >= (int64_t)g.H * g.W;
     AdjCfg cfg;
-    bool ok = false;
-    for (int TH = 32; TH >= 1 && !ok; TH >>= 1) ok = adj_config(g, p, TH, cfg);
-    if (!ok) return RS_ERR_UNSUPPORTED;
+    if (!two_pass) {
+        bool ok = false;
+        for (int TH = 32; TH >= 1 && !ok; TH >>= 1) ok = adj_config(g, p, TH, cfg);
+        if (!ok) return RS_ERR_UNSUPPORTED;
+    }
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
@@ -394,6 +470,24 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     const float* dY = static_cast<const float*>(grad_out);
     float* dX = static_cast<float*>(grad_in);
+    if (two_pass) {
+        float* T = reinterpret_cast<float*>(ws + p.off_t);
+        const int rpt = 8;
+        const unsigned gx = (unsigned)(((int64_t)g.W * g.C + kAdjThreads - 1) / kAdjThreads);
+        for (int p0 = 0; p0 < g.planes; p0 += p.group_planes) {
+            const int np = std::min(p.group_planes, g.planes - p0);
+            dim3 gxg(gx, (unsigned)((g.Ho + rpt - 1) / rpt), (unsigned)np);
+            if (KX <= 4) k_adj_x<4><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
+            else if (KX <= 8) k_adj_x<8><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
+            else if (KX <= 16) k_adj_x<16><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
+            else k_adj_x<32><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+            dim3 gyg(gx, (unsigned)((g.H + rpt - 1) / rpt), (unsigned)np);
+            k_adj_y<<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        }
+        return RS_OK;
+    }
     if (KX <= 4) e = launch_adj_c<4>(g, dY, dX, tb, cfg, st);
     else if (KX <= 8) e = launch_adj_c<8>(g, dY, dX, tb, cfg, st);
     else if (KX <= 16) e = launch_adj_c<16>(g, dY, dX, tb, cfg, st);

@@ -32,11 +32,12 @@ SHAPES = [(37, 53, 74, 106), (64, 48, 32, 24), (31, 29, 53, 71), (40, 40, 40, 40
 
 @pytest.mark.parametrize("method", [0, 1, 2])
 @pytest.mark.parametrize("coord", [0, 1])
-def test_adjoint_nchw_matches_oracle(rs, oracle, method, coord):
+@pytest.mark.parametrize("impl", ["auto", "tiled"])
+def test_adjoint_nchw_matches_oracle(rs, oracle, method, coord, impl):
     for k, (H, W, Ho, Wo) in enumerate(SHAPES):
         g = np.random.default_rng(100 + k).standard_normal((2, 3, Ho, Wo)).astype(np.float32)
         gt = torch.from_numpy(g).cuda()
-        gi = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord])
+        gi = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord], impl=impl)
         torch.cuda.synchronize()
         ref = oracle.adjoint_nchw(g.astype(np.float64), H, W, method, coord)
         err = np.abs(gi.cpu().numpy().astype(np.float64) - ref).max()
@@ -46,11 +47,12 @@ def test_adjoint_nchw_matches_oracle(rs, oracle, method, coord):
 
 
 @pytest.mark.parametrize("C", [1, 3, 4])
-def test_adjoint_hwc_matches_oracle(rs, oracle, C):
+@pytest.mark.parametrize("impl", ["auto", "tiled"])
+def test_adjoint_hwc_matches_oracle(rs, oracle, C, impl):
     for method in (1, 2):
         H, W, Ho, Wo = 45, 61, 97, 130
         g = np.random.default_rng(7).standard_normal((Ho, Wo, C)).astype(np.float32)
-        gi = rs.resize_backward(torch.from_numpy(g).cuda(), (H, W), MN[method], layout="hwc")
+        gi = rs.resize_backward(torch.from_numpy(g).cuda(), (H, W), MN[method], layout="hwc", impl=impl)
         torch.cuda.synchronize()
         ref = oracle.adjoint(g.astype(np.float64), H, W, method)
         tol = _tol(oracle, H, W, Ho, Wo, method, 0, np.abs(g).max())
@@ -131,3 +133,19 @@ def test_workspace_errors(rs):
     s = B.lib().rs_resize_backward(g.data_ptr(), ctypes.byref(Lo), x.data_ptr(), ctypes.byref(Li), B.RS_U8, 1,
                                    ctypes.byref(o), None, 0, st)
     assert s == B.RS_ERR_UNSUPPORTED
+
+
+def test_plane_groups_and_large_upscale(rs, oracle):
+    """More planes than one intermediate group holds, and a x6 upscale
+    (wide transposed rows)."""
+    g = torch.randn(40, 3, 600, 700, device="cuda")      # 120 planes of 600x700 -> groups
+    gi = rs.resize_backward(g, (300, 350), "bicubic")
+    torch.cuda.synchronize()
+    for (n, c) in ((0, 0), (39, 2), (17, 1)):
+        ref = oracle.adjoint(g[n, c].cpu().numpy().astype(np.float64), 300, 350, 2)[:, :, 0]
+        tol = _tol(oracle, 300, 350, 600, 700, 2, 0, float(g[n, c].abs().max()))
+        assert np.abs(gi[n, c].cpu().numpy() - ref).max() <= tol
+    g6 = torch.randn(1, 1, 120, 180, device="cuda")
+    gi6 = rs.resize_backward(g6, (20, 30), "bicubic", coord="half_pixel")
+    ref = oracle.adjoint(g6[0, 0].cpu().numpy().astype(np.float64), 20, 30, 2, 1)[:, :, 0]
+    assert np.abs(gi6[0, 0].cpu().numpy() - ref).max() <= _tol(oracle, 20, 30, 120, 180, 2, 1, float(g6.abs().max()))
