@@ -33,7 +33,7 @@ static constexpr int kPolyElems = 4 * kPolyThreads;   // strip width in elements
 // 16-byte load units in flight per thread (kPolyPrefetch in the kernel):
 // uint8 units hold 16 elements, so two cover a chunk of staged rows; wider
 // types use four.
-static constexpr int kPolyMaxBand = 1024;             // rows of the row-tap table
+static constexpr int kPolyMaxBand = 256;              // rows of the row-tap table
 
 __device__ __forceinline__ uint32_t poly_pack_u8x4(float2 a, float2 b)
 {
