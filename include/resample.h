@@ -186,6 +186,22 @@ typedef struct {
     int64_t src_pitch, dst_pitch;
 } rs_image_desc;
 
+/*
+ * Batch options (rs_options): coord and cubic_a apply to every image.
+ * impl = RS_IMPL_AUTO: bilinear / bicubic images whose source footprint
+ *   fits run as register-window items (bands of 256 output rows, source
+ *   rows staged 8 at a time, else 4), the rest as tiles; when
+ *   rs_autotune_batched has tuned this batch (same sizes, methods, pitches,
+ *   dtype, count and coord) its shape is used instead. An explicit tile_w /
+ *   tile_h / threads tiles every image.
+ * impl = RS_IMPL_WINDOW: window items with band = tile_w output rows
+ *   (1..256, 0 = 256) and chunk = tile_h staged rows (4..32, 0 = 8 else 4);
+ *   images that do not fit are tiled.
+ * impl = RS_IMPL_TILED: every image as tiles of tile_w elements (0 = 512)
+ *   x at most tile_h rows (0 = 32) with `threads` threads (0 = 256).
+ * Other impl values return RS_ERR_INVALID_ARG.
+ */
+
 /* Device workspace bytes rs_resize_batched needs for these descriptors. */
 rs_status rs_resize_batched_workspace(const rs_image_desc* d, int n, rs_dtype dtype,
                                       size_t* bytes);
@@ -258,6 +274,22 @@ typedef struct {
 rs_status rs_autotune(const void* src, const rs_layout* in, void* dst,
                       const rs_layout* out, rs_dtype dtype, rs_method method,
                       const rs_options* opt, void* stream, rs_tile_config* best);
+/*
+ * Batch autotuner: runs the batch (dst buffers are written; the stream is
+ * synchronised while it runs) for each item shape in a small sweep -- band
+ * heights 32..256 and chunk heights 8 / 4 of the window items, and all
+ * tiles -- and stores the fastest in the same cache under a key made of the
+ * GPU, dtype, image count, coord and a hash of every descriptor's sizes,
+ * channels, method and pitches. Later RS_IMPL_AUTO batch calls (direct or
+ * plans) with that key use it; rs_resize_batched_noalloc does not consult
+ * the cache. best: impl (RS_IMPL_WINDOW or RS_IMPL_TILED), tile_w = band
+ * rows, tile_h = chunk rows (0 = 8 else 4), the chosen and the default
+ * shape's mean time per batch launch, and the number of shapes timed.
+ * `workspace` as for rs_resize_batched.
+ */
+rs_status rs_autotune_batched(const rs_image_desc* d, int n, rs_dtype dtype, void* workspace,
+                              size_t workspace_bytes, const rs_options* opt, void* stream,
+                              rs_tile_config* best);
 rs_status rs_tune_cache_save(const char* path);
 rs_status rs_tune_cache_load(const char* path);
 void rs_tune_cache_clear(void);

@@ -28,7 +28,7 @@ IMPL_NAMES = {v: k for k, v in IMPLS.items()}
 DTYPES = {torch.uint8: B.RS_U8, torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16,
           torch.float32: B.RS_F32}
 
-__all__ = ["resize", "resize_backward", "ResizeFn", "resize_batched", "BatchedPlan", "autotune",
+__all__ = ["resize", "resize_backward", "ResizeFn", "resize_batched", "BatchedPlan", "autotune", "autotune_batched",
            "tile_config", "tune_cache_save", "tune_cache_load", "tune_cache_clear", "debug_fault",
            "version", "lib", "ResampleError", "METHODS", "COORDS"]
 
@@ -219,8 +219,11 @@ def batched_workspace_bytes(srcs, dsts, methods) -> int:
 
 
 def resize_batched(srcs: Sequence[torch.Tensor], sizes, methods, *, coord="asymmetric",
-                   cubic_a: float = -0.5, outs=None, workspace: torch.Tensor | None = None):
-    """Resample a ragged list of (H, W, C) images in one persistent launch."""
+                   cubic_a: float = -0.5, outs=None, workspace: torch.Tensor | None = None,
+                   impl: str = "auto", tile=None, threads: int = 0):
+    """Resample a ragged list of (H, W, C) images in one persistent launch.
+    impl="window": tile = (band rows, chunk rows) of the window items;
+    impl="tiled": tile = (elements, rows) of every image's tiles."""
     _require_cuda(*srcs)
     if outs is None:
         outs = [torch.empty((int(h), int(w), s.shape[2]), dtype=s.dtype, device=s.device)
@@ -231,7 +234,7 @@ def resize_batched(srcs: Sequence[torch.Tensor], sizes, methods, *, coord="asymm
     B.check(lib().rs_resize_batched_workspace(arr, n, dt, ctypes.byref(nb)), "rs_resize_batched_workspace")
     if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
-    o = _opts(coord, cubic_a, "auto", None, 0)
+    o = _opts(coord, cubic_a, impl, tile, threads)
     with torch.cuda.device(srcs[0].device):
         B.check(lib().rs_resize_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),
                                         _stream(srcs[0])), "rs_resize_batched")
@@ -242,7 +245,8 @@ class BatchedPlan:
     """A ragged batch recorded once (work list uploaded, persistent launch
     captured as a CUDA graph) and replayed by launch()."""
 
-    def __init__(self, srcs, outs, methods, *, coord="asymmetric", cubic_a: float = -0.5):
+    def __init__(self, srcs, outs, methods, *, coord="asymmetric", cubic_a: float = -0.5,
+                 impl: str = "auto", tile=None, threads: int = 0):
         _require_cuda(*srcs, *outs)
         self.srcs, self.outs = list(srcs), list(outs)
         arr, n = _descs(self.srcs, self.outs, methods)
@@ -250,7 +254,7 @@ class BatchedPlan:
         dt = _dtype(srcs[0])
         B.check(lib().rs_resize_batched_workspace(arr, n, dt, ctypes.byref(nb)), "rs_resize_batched_workspace")
         self.workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
-        o = _opts(coord, cubic_a, "auto", None, 0)
+        o = _opts(coord, cubic_a, impl, tile, threads)
         self._plan = ctypes.c_void_p()
         self.device = srcs[0].device
         with torch.cuda.device(self.device):
@@ -292,6 +296,26 @@ def autotune(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric",
     return {"impl": IMPL_NAMES.get(best.impl, best.impl), "tile_w": best.tile_w, "tile_h": best.tile_h,
             "threads": best.threads, "waves": best.waves, "best_us": best.best_us,
             "default_us": best.default_us, "candidates": best.candidates}
+
+
+def autotune_batched(srcs, outs, methods, *, coord="asymmetric", cubic_a: float = -0.5,
+                     workspace: torch.Tensor | None = None) -> dict:
+    """Time the batch at each item shape and cache the fastest for later
+    batch calls on the same descriptors (the outputs are written)."""
+    _require_cuda(*srcs, *outs)
+    arr, n = _descs(srcs, outs, methods)
+    nb = ctypes.c_size_t(0)
+    dt = _dtype(srcs[0])
+    B.check(lib().rs_resize_batched_workspace(arr, n, dt, ctypes.byref(nb)), "rs_resize_batched_workspace")
+    if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
+        workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
+    o = _opts(coord, cubic_a, "auto", None, 0)
+    best = B.RsTileConfig()
+    with torch.cuda.device(srcs[0].device):
+        B.check(lib().rs_autotune_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),
+                                          _stream(srcs[0]), ctypes.byref(best)), "rs_autotune_batched")
+    return {"impl": IMPL_NAMES.get(best.impl, best.impl), "band": best.tile_w, "chunk": best.tile_h,
+            "best_us": best.best_us, "default_us": best.default_us, "candidates": best.candidates}
 
 
 def tile_config(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric", cubic_a=-0.5) -> dict:

@@ -73,6 +73,8 @@ SIGNATURES = {
     "rs_batched_plan_destroy": (I32, [P]),
     "rs_autotune": (I32, [P, ctypes.POINTER(RsLayout), P, ctypes.POINTER(RsLayout), I32, I32,
                           ctypes.POINTER(RsOptions), P, ctypes.POINTER(RsTileConfig)]),
+    "rs_autotune_batched": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, P, SZ, ctypes.POINTER(RsOptions), P,
+                                  ctypes.POINTER(RsTileConfig)]),
     "rs_tune_cache_save": (I32, [ctypes.c_char_p]),
     "rs_tune_cache_load": (I32, [ctypes.c_char_p]),
     "rs_tune_cache_clear": (None, []),

@@ -19,13 +19,10 @@
 
 namespace rs {
 
-struct Tuned {
-    int impl, tile_w, tile_h, threads, waves;
-};
-
 static std::mutex g_tune_mu;
 static std::map<std::string, Tuned> g_tune;
 static bool g_env_loaded = false;
+static void load_env_once();
 
 static int scale_class(int n, int m)
 {
@@ -42,10 +39,26 @@ static std::string tune_key(const Geom& g, int method, int dtype)
     return buf;
 }
 
+bool tune_lookup(const std::string& key, Tuned& t)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_env_once();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    t = it->second;
+    return true;
+}
+
+void tune_store(const std::string& key, const Tuned& t)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = t;
+}
+
 static bool valid_tuned(const Tuned& t)
 {
     if (t.impl == RS_IMPL_GATHER) return t.tile_w > 0 && t.tile_h > 0;
-    if (t.impl == RS_IMPL_WINDOW) return t.tile_h > 0 && t.waves > 0;
+    if (t.impl == RS_IMPL_WINDOW) return t.tile_h >= 0 && t.tile_w > 0 && (t.waves > 0 || t.tile_w <= 256);
     if (t.impl == RS_IMPL_STREAM) return t.tile_w > 0 && t.tile_h > 0 && t.waves > 0;
     if (t.impl == RS_IMPL_TILED) return t.tile_w > 0 && t.tile_h > 0 && (t.threads == 128 || t.threads == 256);
     return false;

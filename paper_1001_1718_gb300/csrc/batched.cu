@@ -169,11 +169,20 @@ static bool image_tile(const Geom& g, int method, int tile_w, int h_cap, int thr
     return false;
 }
 
+// Shape of a batch's items: every image as tiles, or bilinear / bicubic
+// images as register-window items of `band` output rows whose source rows
+// are staged `chunk` at a time (chunk 0: 8, else 4 when 8 does not fit).
+struct BatchShape {
+    bool tiled;
+    int chunk, band;
+};
+
 // Validates one descriptor and fills its device descriptor: window items
-// (bilinear / bicubic, footprint within ~100 KB of shared memory, default
-// shapes) or tiles. Returns the class, item count and shared-memory need.
-static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_options& o, int tile_w, int h_cap,
-                               int threads, BatchImage& im, int& cls, int64_t& items, size_t& smem)
+// (bilinear / bicubic, footprint within ~100 KB of shared memory) or tiles.
+// Returns the class, item count and shared-memory need.
+static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_options& o, const BatchShape& sh,
+                               int tile_w, int h_cap, int threads, BatchImage& im, int& cls, int64_t& items,
+                               size_t& smem)
 {
     const int64_t es = (int64_t)dtype_size(dtype);
     if (!x.src || !x.dst) return RS_ERR_INVALID_ARG;
@@ -192,14 +201,16 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
     im.src = x.src; im.dst = x.dst;
     im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
     im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
-    if (x.method != RS_NEAREST && !o.tile_w && !o.tile_h && !o.threads) {
-        for (int ch : {8, 4}) {
+    if (x.method != RS_NEAREST && !sh.tiled) {
+        const int chunks[2] = {sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4};
+        for (int ch : chunks) {
+            if (!ch) continue;
             PolyCfg pc{};
             pc.chunk = ch;
             if (!poly_config(g, x.method, dtype, x.src, pc) || pc.smem > 100 * 1024) continue;
             im.kind = 1;
             im.chunk = pc.chunk;
-            im.band_h = std::min(pc.band_cap, 256);
+            im.band_h = std::min(pc.band_cap, sh.band);
             im.w_swe_max = pc.swe_max;
             im.band_cap = pc.band_cap;
             im.pos_cap = pc.pos_cap;
@@ -238,16 +249,69 @@ struct BatchLayout {
 
 // Fills imgs_out (n entries) and start_out (n + kClasses entries) grouped
 // by class, with no allocation (scratch arrays are caller-provided, n each).
-static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs_options& o, BatchImage* imgs_out,
-                              int64_t* start_out, BatchImage* tmp_imgs, int* tmp_cls, int64_t* tmp_items,
-                              BatchLayout& L)
+// Tuning-cache key of a batch: GPU (SM count), dtype, count, coordinate map
+// and a hash of every descriptor's sizes, channels, method and pitches.
+static std::string batch_key(const rs_image_desc* d, int n, int dtype, const rs_options& o)
+{
+    uint64_t h = 1469598103934665603ull;   // FNV-1a
+    auto mix = [&](int64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint64_t)(v >> (8 * i)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    for (int k = 0; k < n; ++k) {
+        mix(d[k].H); mix(d[k].W); mix(d[k].C); mix(d[k].Ho); mix(d[k].Wo);
+        mix(d[k].method); mix(d[k].src_pitch); mix(d[k].dst_pitch);
+    }
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "sms=%d;batch;dt=%d;n=%d;coord=%d;h=%016llx", num_sms(), dtype, n, o.coord,
+                  (unsigned long long)h);
+    return buf;
+}
+
+// Item shape from the options: RS_IMPL_TILED (or an explicit tile shape with
+// RS_IMPL_AUTO) tiles every image; RS_IMPL_WINDOW takes band = tile_w
+// (default 256) and chunk = tile_h (default 0); RS_IMPL_AUTO takes the
+// tuned shape of this batch when the cache has one (`tuned`), else the
+// default window shape. Other kernels have no batched form.
+static rs_status batch_shape(const rs_image_desc* d, int n, int dtype, const rs_options& o, bool tuned,
+                             BatchShape& sh)
+{
+    const bool explicit_shape = o.tile_w || o.tile_h || o.threads;
+    if (o.impl == RS_IMPL_TILED || (o.impl == RS_IMPL_AUTO && explicit_shape)) {
+        sh = BatchShape{true, 0, 0};
+        return RS_OK;
+    }
+    if (o.impl == RS_IMPL_WINDOW) {
+        sh = BatchShape{false, o.tile_h, o.tile_w ? o.tile_w : kPolyMaxBand};
+        if (sh.chunk && (sh.chunk < 4 || sh.chunk > 32)) return RS_ERR_INVALID_ARG;
+        if (sh.band < 1 || sh.band > kPolyMaxBand) return RS_ERR_INVALID_ARG;
+        return RS_OK;
+    }
+    if (o.impl != RS_IMPL_AUTO) return RS_ERR_INVALID_ARG;
+    sh = BatchShape{false, 0, kPolyMaxBand};
+    Tuned t;
+    if (tuned && tune_lookup(batch_key(d, n, dtype, o), t)) {
+        if (t.impl == RS_IMPL_TILED) sh = BatchShape{true, 0, 0};
+        else if (t.impl == RS_IMPL_WINDOW && t.tile_w >= 1 && t.tile_w <= kPolyMaxBand) sh = BatchShape{false, t.tile_h, t.tile_w};
+    }
+    return RS_OK;
+}
+
+static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs_options& o, bool tuned,
+                              BatchImage* imgs_out, int64_t* start_out, BatchImage* tmp_imgs, int* tmp_cls,
+                              int64_t* tmp_items, BatchLayout& L)
 {
     if (!d || n < 1) return RS_ERR_INVALID_ARG;
     if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
     rs_status s = check_options(o, RS_BILINEAR);
     if (s != RS_OK) return s;
-    const int tile_w = o.tile_w ? o.tile_w : 512;
-    const int h_cap = o.tile_h ? o.tile_h : 32;
+    BatchShape sh;
+    if ((s = batch_shape(d, n, dtype, o, tuned, sh)) != RS_OK) return s;
+    const bool window_opts = o.impl == RS_IMPL_WINDOW;   // tile_w / tile_h describe the window items
+    const int tile_w = o.tile_w && !window_opts ? o.tile_w : 512;
+    const int h_cap = o.tile_h && !window_opts ? o.tile_h : 32;
     L.threads = o.threads ? o.threads : 256;
     if (L.threads != 128 && L.threads != 256) return RS_ERR_INVALID_ARG;
     L.n = n;
@@ -255,7 +319,7 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
     const int64_t es = (int64_t)dtype_size(dtype);
     for (int k = 0; k < n; ++k) {
         size_t sm = 0;
-        s = prepare_image(d[k], dtype, o, tile_w, h_cap, L.threads, tmp_imgs[k], tmp_cls[k], tmp_items[k], sm);
+        s = prepare_image(d[k], dtype, o, sh, tile_w, h_cap, L.threads, tmp_imgs[k], tmp_cls[k], tmp_items[k], sm);
         if (s != RS_OK) return s;
         L.count[tmp_cls[k]]++;
         L.smem[tmp_cls[k]] = std::max(L.smem[tmp_cls[k]], sm);
@@ -392,7 +456,8 @@ static rs_status batch_prepare(const rs_image_desc* d, int n, int dtype, const r
     std::vector<BatchImage> tmp(n);
     std::vector<int> cls(n);
     std::vector<int64_t> items(n);
-    rs_status s = batch_layout(d, n, dtype, o, P.imgs.data(), P.start.data(), tmp.data(), cls.data(), items.data(), P.L);
+    rs_status s = batch_layout(d, n, dtype, o, true, P.imgs.data(), P.start.data(), tmp.data(), cls.data(),
+                               items.data(), P.L);
     if (s != RS_OK) return s;
     P.off_start = align256(sizeof(BatchImage) * (size_t)n);
     P.ws_bytes = P.off_start + sizeof(int64_t) * P.start.size();
@@ -458,7 +523,7 @@ extern "C" rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs
     if (n > kNoAllocMaxImages) return RS_ERR_WORKSPACE;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     BatchLayout L;
-    rs_status s = batch_layout(d, n, dtype, o, g_noalloc_imgs, g_noalloc_start, g_noalloc_tmp, g_noalloc_cls,
+    rs_status s = batch_layout(d, n, dtype, o, false, g_noalloc_imgs, g_noalloc_start, g_noalloc_tmp, g_noalloc_cls,
                                g_noalloc_items, L);
     if (s != RS_OK) return s;
     int dev = 0;
@@ -588,6 +653,81 @@ rs_status rs_batched_plan_destroy(rs_batched_plan* plan)
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     delete plan;
+    return RS_OK;
+}
+
+rs_status rs_autotune_batched(const rs_image_desc* d, int n, rs_dtype dtype, void* workspace,
+                              size_t workspace_bytes, const rs_options* opt, void* stream, rs_tile_config* best)
+{
+    if (!best) return RS_ERR_INVALID_ARG;
+    rs_options o = options_or_default(opt);
+    o.impl = RS_IMPL_AUTO;
+    o.tile_w = o.tile_h = o.threads = o.waves = 0;
+    struct Cand {
+        int impl, band, chunk;
+    };
+    // The default shape first, then band heights x chunk heights, then tiles.
+    const Cand cands[] = {{RS_IMPL_WINDOW, 256, 0}, {RS_IMPL_WINDOW, 128, 0}, {RS_IMPL_WINDOW, 64, 0},
+                          {RS_IMPL_WINDOW, 32, 0},  {RS_IMPL_WINDOW, 256, 4}, {RS_IMPL_WINDOW, 128, 4},
+                          {RS_IMPL_WINDOW, 64, 4},  {RS_IMPL_TILED, 0, 0}};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaError_t e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    rs_status result = RS_OK;
+    float best_us = 0.0f, default_us = 0.0f;
+    int best_i = -1, timed = 0;
+    for (int i = 0; i < (int)(sizeof cands / sizeof cands[0]) && e == cudaSuccess; ++i) {
+        rs_options oc = o;
+        oc.impl = cands[i].impl;
+        oc.tile_w = cands[i].band;
+        oc.tile_h = cands[i].chunk;
+        BatchPlanHost P;
+        rs_status s = batch_prepare(d, n, dtype, oc, P);
+        if (s == RS_OK) s = check_ws(P, workspace, workspace_bytes);
+        if (s != RS_OK) {
+            if (i == 0) { result = s; break; }   // the default shape must be valid
+            continue;
+        }
+        if ((e = upload(P, workspace, st)) != cudaSuccess) break;
+        ClassLaunch cls[kClasses];
+        int nl = 0;
+        if ((e = class_launches(P.L, dtype, oc, workspace, static_cast<char*>(workspace) + P.off_start, cls, nl)) !=
+            cudaSuccess)
+            break;
+        // One untimed launch, then the mean of three.
+        if ((e = launch_classes(cls, nl, st)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev0, st)) != cudaSuccess) break;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_classes(cls, nl, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+        if (e != cudaSuccess) break;
+        const float us = ms * 1000.0f / 3.0f;
+        ++timed;
+        if (i == 0) default_us = us;
+        if (best_i < 0 || us < best_us) {
+            best_i = i;
+            best_us = us;
+        }
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (result != RS_OK) return result;
+    const Cand& c = cands[best_i];
+    // Tiled batches are stored with the batch's tile defaults (512 x 32).
+    const Tuned t = c.impl == RS_IMPL_TILED ? Tuned{RS_IMPL_TILED, 512, 32, 256, 0} : Tuned{c.impl, c.band, c.chunk, 256, 0};
+    tune_store(batch_key(d, n, dtype, o), t);
+    best->impl = c.impl;
+    best->tile_w = c.band;
+    best->tile_h = c.chunk;
+    best->threads = 256;
+    best->waves = 0;
+    best->best_us = best_us;
+    best->default_us = default_us;
+    best->candidates = timed;
     return RS_OK;
 }
 

@@ -1,6 +1,8 @@
 // Host-side helpers shared by the C ABI translation units.
 #pragma once
 
+#include <string>
+
 #include "../../include/resample.h"
 #include "rs_internal.h"
 
@@ -37,5 +39,12 @@ cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src,
                           const KernelChoice& k, cudaStream_t st);
 
 cudaError_t read_fault(cudaStream_t st, unsigned int* code);
+
+// Tuning cache entry: kernel (rs_impl) and shape; see autotune.cpp.
+struct Tuned {
+    int impl, tile_w, tile_h, threads, waves;
+};
+bool tune_lookup(const std::string& key, Tuned& t);
+void tune_store(const std::string& key, const Tuned& t);
 
 }  // namespace rs

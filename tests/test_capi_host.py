@@ -106,6 +106,24 @@ def test_layout_validation(L):
                           ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
 
 
+def test_batched_options_validation(L):
+    """Batch calls reject kernels with no batched form and window shapes
+    out of range on the host, before the work list is uploaded."""
+    from paper_1001_1718_gb300 import _binding as B
+    arr = (B.RsImageDesc * 1)()
+    d = arr[0]
+    d.src, d.dst = 0x10000, 0x90000000      # never dereferenced: validation fails first
+    d.H, d.W, d.C, d.Ho, d.Wo, d.method = 8, 8, 3, 16, 16, B.RS_BICUBIC
+    d.src_pitch, d.dst_pitch = 24, 48
+    ws = 0x20000000
+    for o in (B.options(impl=B.RS_IMPL_STREAM), B.options(impl=B.RS_IMPL_GATHER), B.options(impl=B.RS_IMPL_PLAIN),
+              B.options(impl=B.RS_IMPL_WINDOW, tile_w=257), B.options(impl=B.RS_IMPL_WINDOW, tile_h=2),
+              B.options(impl=B.RS_IMPL_WINDOW, tile_h=33)):
+        assert L.rs_resize_batched(arr, 1, B.RS_U8, ws, 1 << 20, ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
+        assert L.rs_resize_batched_noalloc(arr, 1, B.RS_U8, ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
+    assert L.rs_autotune_batched(arr, 1, B.RS_U8, ws, 1 << 20, None, None, None) == B.RS_ERR_INVALID_ARG
+
+
 def test_tune_cache_file_roundtrip(L, tmp_path):
     p = tmp_path / "tune.txt"
     key = "sms=152;dt=0;m=2;C=3;coord=0;sy=4;sx=4;sz=27"
@@ -131,10 +149,13 @@ def test_tile_config_query_without_buffers(L):
     from paper_1001_1718_gb300 import _binding as B
     Li, Lo = L.rs_layout_hwc(1, 4096, 4096, 3), L.rs_layout_hwc(1, 8192, 8192, 3)
     c = B.RsTileConfig()
-    # num_sms() falls back to 1 without a GPU; the choice itself is host logic
+    # Without a GPU, num_sms() falls back to 1 and the shared-memory limit to
+    # 48 KB; the choice itself is host logic: a large upscale runs the
+    # register-window kernel (chunks of 8 staged rows on a GB300, 4 within
+    # the 48 KB fallback).
     assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_U8, B.RS_BICUBIC, None,
                                 ctypes.byref(c)) == 0
-    assert c.impl == B.RS_IMPL_STREAM and c.tile_w > 0 and c.tile_h > 0
+    assert c.impl == B.RS_IMPL_WINDOW and c.tile_w == 1024 and c.tile_h in (4, 8)
     del rs
 
 

@@ -109,3 +109,31 @@ def test_full_batch_workload(rs, oracle):
         if k % 16 == 0:
             assert torch.equal(y, rs.resize(srcs[k], sizes[k], methods[k]))
     assert rs.debug_fault() == 0
+
+
+def test_batch_item_shapes_agree(rs):
+    """Window items of any band / chunk height and plain tiles compute each
+    output element with the same operations: every shape gives the same
+    bytes as the default; tuning picks one of them and changes nothing."""
+    srcs, sizes, methods, _ = _batch(9, 20)
+    ref = rs.resize_batched(srcs, sizes, methods)
+    for impl, tile in (("window", (1, 0)), ("window", (32, 4)), ("window", (256, 8)), ("window", (77, 16)),
+                       ("tiled", None), ("tiled", (256, 8))):
+        got = rs.resize_batched(srcs, sizes, methods, impl=impl, tile=tile)
+        assert all(torch.equal(a, b) for a, b in zip(got, ref)), (impl, tile)
+    outs = [torch.empty_like(y) for y in ref]
+    best = rs.autotune_batched(srcs, outs, methods)
+    assert best["impl"] in ("window", "tiled") and best["candidates"] >= 2
+    assert best["best_us"] > 0 and best["best_us"] <= best["default_us"]
+    assert all(torch.equal(a, b) for a, b in zip(outs, ref))
+    plan = rs.BatchedPlan(srcs, [torch.zeros_like(y) for y in ref], methods)   # uses the tuned shape
+    plan.launch()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(plan.outs, ref))
+    plan.close()
+    with pytest.raises(rs.ResampleError):
+        rs.resize_batched(srcs, sizes, methods, impl="stream")
+    with pytest.raises(rs.ResampleError):
+        rs.resize_batched(srcs, sizes, methods, impl="window", tile=(300, 8))
+    rs.tune_cache_clear()
+    assert rs.debug_fault() == 0
