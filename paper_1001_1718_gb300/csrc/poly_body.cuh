@@ -1,8 +1,9 @@
 // Register-window resampling (bilinear / bicubic): the per-block work.
 //
 // A block owns a strip of tile_w = 4 * 256 output elements and a band of
-// output rows; thread t owns strip elements 4t .. 4t+3 for the whole band
-// and walks down it. Output row i of the band takes source rows
+// output rows; thread t owns strip elements t, t + 256, t + 512 and t + 768
+// for the whole band and walks down it (consecutive lanes then gather
+// neighbouring source elements: no shared-memory bank conflicts). Output row i of the band takes source rows
 // f(i), ..., f(i) + KT - 1 (its first tap f(i) never decreases with i), so
 // the thread keeps the horizontally interpolated values of the last KT
 // source rows in registers and advances a source-row position b:
@@ -47,41 +48,47 @@ __device__ __forceinline__ uint32_t poly_pack_u8x4(float2 a, float2 b)
     return out;
 }
 
+// Stores a thread's four outputs (a.x, a.y, b.x, b.y) at p, p + 256,
+// p + 512 and p + 768; only the first `nact` exist (ragged strip end).
 template <typename T>
-__device__ __forceinline__ void poly_store4(T* p, float2 a, float2 b, int cnt)
+__device__ __forceinline__ void poly_store_strided(T* p, float2 a, float2 b, int nact)
 {
-    if (cnt == 4) {
-        if constexpr (sizeof(T) == 1) {
-            if ((reinterpret_cast<uintptr_t>(p) & 3) == 0) {
-                *reinterpret_cast<uint32_t*>(p) = poly_pack_u8x4(a, b);
-                return;
-            }
-        } else if constexpr (sizeof(T) == 2) {
-            if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
-                uint2 w;
-                if constexpr (std::is_same<T, __half>::value) {
-                    __half2 h0 = __float22half2_rn(a), h1 = __float22half2_rn(b);
-                    w.x = *reinterpret_cast<uint32_t*>(&h0);
-                    w.y = *reinterpret_cast<uint32_t*>(&h1);
-                } else {
-                    __nv_bfloat162 h0 = __float22bfloat162_rn(a), h1 = __float22bfloat162_rn(b);
-                    w.x = *reinterpret_cast<uint32_t*>(&h0);
-                    w.y = *reinterpret_cast<uint32_t*>(&h1);
-                }
-                *reinterpret_cast<uint2*>(p) = w;
-                return;
-            }
+    constexpr int S = kPolyThreads;
+    if constexpr (sizeof(T) == 1) {
+        const uint32_t w = poly_pack_u8x4(a, b);
+        uint8_t* q = reinterpret_cast<uint8_t*>(p);
+        if (nact == 4) {
+            q[0] = (uint8_t)w;
+            q[S] = (uint8_t)(w >> 8);
+            q[2 * S] = (uint8_t)(w >> 16);
+            q[3 * S] = (uint8_t)(w >> 24);
         } else {
-            if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-                *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
-                return;
-            }
+            #pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k < nact) q[k * S] = (uint8_t)(w >> (8 * k));
         }
+    } else if constexpr (sizeof(T) == 2) {
+        uint32_t lo, hi;
+        if constexpr (std::is_same<T, __half>::value) {
+            __half2 h0 = __float22half2_rn(a), h1 = __float22half2_rn(b);
+            lo = *reinterpret_cast<uint32_t*>(&h0);
+            hi = *reinterpret_cast<uint32_t*>(&h1);
+        } else {
+            __nv_bfloat162 h0 = __float22bfloat162_rn(a), h1 = __float22bfloat162_rn(b);
+            lo = *reinterpret_cast<uint32_t*>(&h0);
+            hi = *reinterpret_cast<uint32_t*>(&h1);
+        }
+        uint16_t* q = reinterpret_cast<uint16_t*>(p);
+        const uint16_t v[4] = {(uint16_t)lo, (uint16_t)(lo >> 16), (uint16_t)hi, (uint16_t)(hi >> 16)};
+        #pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < nact) q[k * S] = v[k];
+    } else {
+        const float v[4] = {a.x, a.y, b.x, b.y};
+        #pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < nact) p[k * S] = v[k];
     }
-    const float v[4] = {a.x, a.y, b.x, b.y};
-    #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < cnt) Store<T>::put(p + k, v[k]);
 }
 
 template <typename T>
@@ -176,16 +183,16 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
         for (int p = 0; p < KT; ++p) RW[i * KT + p] = w[p];
     }
 
-    // Column taps of this thread's four elements.
-    const bool active = 4 * tid < nE;
-    const int cnt = min(4, nE - 4 * tid);
+    // Column taps of this thread's four elements tid + 256 k (the first
+    // nact of them lie inside the strip).
+    const int nact = max(0, min(4, (nE - tid + kPolyThreads - 1) / kPolyThreads));
     int off[4];
     float2 w01[KT], w23[KT];
     {
         float wx[4][KT];
         #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int el = 4 * tid + k;
+            const int el = tid + kPolyThreads * k;
             if (el < nE) {
                 const int64_t e = e0 + el;
                 const int j = (int)(e / C), c = (int)(e - (int64_t)j * C);
@@ -346,7 +353,7 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
         }
     };
     auto put = [&](int row, float2 v01, float2 v23) {
-        if (active) poly_store4<T>(d + (int64_t)(yb + row) * g.dst_pitch + e0 + 4 * tid, v01, v23, cnt);
+        if (nact > 0) poly_store_strided<T>(d + (int64_t)(yb + row) * g.dst_pitch + e0 + tid, v01, v23, nact);
     };
     // Emit the output rows whose first tap is b (two at a time: independent
     // chains), from window slots slot[0..KT).
