@@ -36,18 +36,6 @@ static constexpr int kPolyElems = 4 * kPolyThreads;   // strip width in elements
 // types use four.
 static constexpr int kPolyMaxBand = 256;              // rows of the row-tap table
 
-__device__ __forceinline__ uint32_t poly_pack_u8x4(float2 a, float2 b)
-{
-    const float2 M = make_float2(12582912.0f, 12582912.0f);
-    const float2 ra = __fadd2_rn(a, M), rb = __fadd2_rn(b, M);
-    const int i0 = __float_as_int(ra.x) - 0x4B400000, i1 = __float_as_int(ra.y) - 0x4B400000;
-    const int i2 = __float_as_int(rb.x) - 0x4B400000, i3 = __float_as_int(rb.y) - 0x4B400000;
-    uint32_t hi, out;
-    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(hi) : "r"(i3), "r"(i2), "r"(0u));
-    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(out) : "r"(i1), "r"(i0), "r"(hi));
-    return out;
-}
-
 // Stores a thread's four outputs (a.x, a.y, b.x, b.y) at p, p + 256,
 // p + 512 and p + 768; only the first `nact` exist (ragged strip end).
 template <typename T>
@@ -55,17 +43,16 @@ __device__ __forceinline__ void poly_store_strided(T* p, float2 a, float2 b, int
 {
     constexpr int S = kPolyThreads;
     if constexpr (sizeof(T) == 1) {
-        const uint32_t w = poly_pack_u8x4(a, b);
+        // Round to nearest even and saturate to [0, 255] in one conversion.
+        const float v[4] = {a.x, a.y, b.x, b.y};
         uint8_t* q = reinterpret_cast<uint8_t*>(p);
-        if (nact == 4) {
-            q[0] = (uint8_t)w;
-            q[S] = (uint8_t)(w >> 8);
-            q[2 * S] = (uint8_t)(w >> 16);
-            q[3 * S] = (uint8_t)(w >> 24);
-        } else {
-            #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (k < nact) q[k * S] = (uint8_t)(w >> (8 * k));
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < nact) {
+                unsigned short r;
+                asm("cvt.rni.sat.u8.f32 %0, %1;" : "=h"(r) : "f"(v[k]));
+                q[k * S] = (uint8_t)r;
+            }
         }
     } else if constexpr (sizeof(T) == 2) {
         uint32_t lo, hi;
