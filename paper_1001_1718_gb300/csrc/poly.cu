@@ -2,6 +2,7 @@
 // block per (strip of 1024 output elements, band of output rows, plane);
 // the block's work is poly_body (poly_body.cuh).
 #include <algorithm>
+#include <climits>
 
 #include "capi_internal.h"
 #include "poly_body.cuh"
@@ -42,6 +43,7 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
     const int span_px = poly_span_bound(kpx, g.W, g.Wo, KT);
     c.swe_max = ((span_px * g.C + 2 * EPU + 4) + 3) & ~3;
     c.band_cap = std::min(kPolyMaxBand, g.Ho);
+    if ((int64_t)c.band_cap * g.dst_pitch >= (int64_t)INT32_MAX) return false;   // 32-bit row offsets
     c.pos_cap = poly_span_bound(c.band_cap, g.H, g.Ho, KT);   // source positions of a band
     const size_t tables = sizeof(float) * (2 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KT) +
                           sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);

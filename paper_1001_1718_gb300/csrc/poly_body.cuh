@@ -31,9 +31,6 @@ namespace rs {
 
 static constexpr int kPolyThreads = 256;
 static constexpr int kPolyElems = 4 * kPolyThreads;   // strip width in elements
-// 16-byte load units in flight per thread (kPolyPrefetch in the kernel):
-// uint8 units hold 16 elements, so two cover a chunk of staged rows; wider
-// types use four.
 static constexpr int kPolyMaxBand = 256;              // rows of the row-tap table
 
 // Stores a thread's four outputs (a.x, a.y, b.x, b.y) at p, p + 256,
@@ -339,8 +336,12 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
             v23 = __ffma2_rn(w2, h23[slot[p]], v23);
         }
     };
+    // Output rows are addressed from the band's first row with 32-bit
+    // offsets (the host bounds band_cap * dst_pitch below 2^31).
+    T* const dband = d + (int64_t)yb * g.dst_pitch + e0 + tid;
+    const int pitch32 = (int)g.dst_pitch;
     auto put = [&](int row, float2 v01, float2 v23) {
-        if (nact > 0) poly_store_strided<T>(d + (int64_t)(yb + row) * g.dst_pitch + e0 + tid, v01, v23, nact);
+        if (nact > 0) poly_store_strided<T>(dband + row * pitch32, v01, v23, nact);
     };
     // Emit the output rows whose first tap is b (two at a time: independent
     // chains), from window slots slot[0..KT).
