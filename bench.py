@@ -51,8 +51,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="tune tile shapes before timing")
-    ap.add_argument("--ops-only", action="store_true",
-                    help="run warmup + steps of the three headline resizes and exit (profiling driver)")
+    ap.add_argument("--ops-only", nargs="?", const="headline", default=None,
+                    choices=["headline", "backward", "batch"],
+                    help="profiling driver: run warmup + steps of the three headline resizes (headline), "
+                         "of the NCHW FP32 backward x2 / x0.5 (backward) or of the 256-image batch plan "
+                         "(batch), and exit")
     return ap.parse_args()
 
 
@@ -248,6 +251,33 @@ def torch_index(a):
     return torch.from_numpy(np.asarray(a, np.int64)).cuda()
 
 
+def profile_ops(args, torch, rs, workloads, dev):
+    """Untimed launches for profiling under ncu: the NCHW FP32 backward
+    (bilinear / bicubic, x2 and x0.5 of 32x3x512x512) or the replayable plan
+    of the 256-image ragged batch."""
+    if args.ops_only == "backward":
+        xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
+        ops = []
+        for method in ("bilinear", "bicubic"):
+            for s in (2.0, 0.5):
+                Ho = int(512 * s)
+                g = torch.randn((32, 3, Ho, Ho), dtype=torch.float32, device=dev)
+                gi = torch.empty_like(xn)
+                ws = torch.empty(rs.backward_workspace_bytes(g, (512, 512), method), dtype=torch.uint8, device=dev)
+                ops.append(lambda g=g, gi=gi, ws=ws, m=method: rs.resize_backward(g, (512, 512), m, grad_in=gi,
+                                                                                 workspace=ws))
+    else:
+        items = workloads.batch_spec(seed=4)
+        srcs = [torch.from_numpy(im).to(dev) for im in workloads.batch_images(items)]
+        outs = [torch.empty((it.Ho, it.Wo, 3), dtype=torch.uint8, device=dev) for it in items]
+        plan = rs.BatchedPlan(srcs, outs, [workloads.METHOD_NAMES[it.method] for it in items])
+        ops = [plan.launch]
+    for _ in range(args.warmup + args.steps):
+        for fn in ops:
+            fn()
+    torch.cuda.synchronize()
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_1001_1718_gb300 as rs
@@ -257,6 +287,10 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(dev)
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream(dev)
+
+    if args.ops_only in ("backward", "batch"):
+        profile_ops(args, torch, rs, workloads, dev)
+        return None
 
     img = workloads.workload_rgb_4096(seed=2)
     H, W, C = img.shape

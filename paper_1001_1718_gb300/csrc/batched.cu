@@ -39,9 +39,14 @@ struct BatchImage {
     int chunk, band_h, w_swe_max, band_cap, pos_cap, vec, raw_row, raw_off;   // kind 1: window config
 };
 
-// Classes: 0..7 = window (KT 2 / 4) x (C 1..4), 8 = tiled.
-static constexpr int kClasses = 9;
-static constexpr int kTileClass = 8;
+// Classes: 0..7 = window (KT 2 / 4) x (C 1..4) with a footprint of at most
+// kWindowSmallSmem bytes of shared memory (three blocks per SM), 8..15 the
+// same with larger footprints (up to ~100 KB, two blocks per SM), 16 =
+// tiled. Splitting by footprint keeps one large image from lowering the
+// occupancy of its whole class.
+static constexpr int kClasses = 17;
+static constexpr int kTileClass = 16;
+static constexpr size_t kWindowSmallSmem = 72 * 1024;
 
 __device__ __forceinline__ int find_image(const int64_t* __restrict__ start, int n, int64_t t)
 {
@@ -220,7 +225,7 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
             im.tiles_x = (int)(((int64_t)x.Wo * x.C + 1023) / 1024);
             items = (int64_t)im.tiles_x * ((x.Ho + im.band_h - 1) / im.band_h);
             smem = pc.smem;
-            cls = (x.method == RS_BILINEAR ? 0 : 4) + (x.C - 1);
+            cls = (pc.smem <= kWindowSmallSmem ? 0 : 8) + (x.method == RS_BILINEAR ? 0 : 4) + (x.C - 1);
             return RS_OK;
         }
     }
@@ -361,7 +366,8 @@ static void* win_func() { return reinterpret_cast<void*>(&k_batched_window<KT, C
 template <typename T>
 static void* class_func_t(int c)
 {
-    switch (c) {
+    if (c == kTileClass) return reinterpret_cast<void*>(&k_batched<T>);
+    switch (c & 7) {
     case 0: return win_func<2, 1, T>();
     case 1: return win_func<2, 2, T>();
     case 2: return win_func<2, 3, T>();
@@ -369,8 +375,7 @@ static void* class_func_t(int c)
     case 4: return win_func<4, 1, T>();
     case 5: return win_func<4, 2, T>();
     case 6: return win_func<4, 3, T>();
-    case 7: return win_func<4, 4, T>();
-    default: return reinterpret_cast<void*>(&k_batched<T>);
+    default: return win_func<4, 4, T>();
     }
 }
 
