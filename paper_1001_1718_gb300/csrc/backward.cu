@@ -21,6 +21,7 @@
 //    transpose. Every dX element is one fixed-order sum, so the result is
 //    deterministic (no atomics).
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "capi_internal.h"
@@ -244,54 +245,93 @@ k_adjoint(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, co
 static constexpr int kAdjThreads = 256;
 
 // T[p][j][e] = sum_k wx[x][k] dY[p][j][(xlo(x) + k) C + c] for the dY rows
-// j of this block (e = x C + c). T has rows of W C elements.
+// j of this block (e = x C + c). T has rows of W C elements. Four dY rows
+// are gathered per iteration (independent loads in flight); row offsets
+// within a plane are 32-bit (the host bounds Ho x pitch below 2^31).
 template <int KXM>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adj_x(const Geom g, const float* __restrict__ dY, float* __restrict__ T, const AdjTables tb, int plane0,
         int rows_per_thread)
 {
-    const int64_t WC = (int64_t)g.W * g.C;
-    const int64_t e = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    const int WC = g.W * g.C;
+    const int e = blockIdx.x * kAdjThreads + threadIdx.x;
     if (e >= WC) return;
     const int pl = blockIdx.z;
-    const int x = (int)(e / g.C), c = (int)(e - (int64_t)x * g.C);
+    const int x = e / g.C, c = e - x * g.C;
     const int lo = __ldg(tb.xlo + x);
     const int cnt = min(__ldg(tb.xcnt + x), KXM);
     float w[KXM];
     #pragma unroll
     for (int k = 0; k < KXM; ++k) w[k] = k < cnt ? __ldg(tb.xw + (int64_t)x * tb.xK + k) : 0.0f;
-    const float* src = dY + g.dp.offset(plane0 + pl) + (int64_t)lo * g.C + c;
+    const float* src = dY + g.dp.offset(plane0 + pl) + lo * g.C + c;
     float* dst = T + (int64_t)pl * g.Ho * WC + e;
+    const int pitch = (int)g.dst_pitch;
     const int j0 = blockIdx.y * rows_per_thread, j1 = min(g.Ho, j0 + rows_per_thread);
-    for (int j = j0; j < j1; ++j) {
-        const float* row = src + (int64_t)j * g.dst_pitch;
+    int j = j0;
+    for (; j + 4 <= j1; j += 4) {
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        #pragma unroll
+        for (int k = 0; k < KXM; ++k) {
+            if (k < cnt) {
+                float v[4];
+                #pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = __ldg(src + (j + r) * pitch + k * g.C);
+                #pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] = fmaf(w[k], v[r], acc[r]);
+            }
+        }
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) dst[(j + r) * WC] = acc[r];
+    }
+    for (; j < j1; ++j) {
+        const float* row = src + j * pitch;
         float acc = 0.0f;
         #pragma unroll
         for (int k = 0; k < KXM; ++k)
-            if (k < cnt) acc = fmaf(w[k], __ldg(row + (int64_t)k * g.C), acc);
-        dst[(int64_t)j * WC] = acc;
+            if (k < cnt) acc = fmaf(w[k], __ldg(row + k * g.C), acc);
+        dst[j * WC] = acc;
     }
 }
 
-// dX[p][i][e] = sum_a wy[i][a] T[p][ylo(i) + a][e] for the dX rows i of
-// this block.
+// dX[p][i][e..e+V-1] = sum_a wy[i][a] T[p][ylo(i) + a][e..e+V-1] for the dX
+// rows i of this block; V = 4 (16-byte loads and stores) when rows allow.
+template <int KYM, int V>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const AdjTables tb, int plane0,
         int rows_per_thread)
 {
-    const int64_t WC = (int64_t)g.W * g.C;
-    const int64_t e = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    const int WC = g.W * g.C;
+    const int e = (blockIdx.x * kAdjThreads + threadIdx.x) * V;
     if (e >= WC) return;
     const int pl = blockIdx.z;
     const float* src = T + (int64_t)pl * g.Ho * WC + e;
     float* dst = dX + g.sp.offset(plane0 + pl) + e;
+    const int pitch = (int)g.src_pitch;
     const int i0 = blockIdx.y * rows_per_thread, i1 = min(g.H, i0 + rows_per_thread);
     for (int i = i0; i < i1; ++i) {
-        const int lo = __ldg(tb.ylo + i), cnt = __ldg(tb.ycnt + i);
+        const int lo = __ldg(tb.ylo + i), cnt = min(__ldg(tb.ycnt + i), KYM);
         const float* wr = tb.yw + (int64_t)i * tb.yK;
-        float acc = 0.0f;
-        for (int a = 0; a < cnt; ++a) acc = fmaf(__ldg(wr + a), __ldg(src + (int64_t)(lo + a) * WC), acc);
-        dst[(int64_t)i * g.src_pitch] = acc;
+        float acc[V];
+        #pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.0f;
+        #pragma unroll
+        for (int a = 0; a < KYM; ++a) {
+            if (a < cnt) {
+                const float wa = __ldg(wr + a);
+                const float* row = src + (lo + a) * WC;
+                if constexpr (V == 4) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(row));
+                    acc[0] = fmaf(wa, t.x, acc[0]);
+                    acc[1] = fmaf(wa, t.y, acc[1]);
+                    acc[2] = fmaf(wa, t.z, acc[2]);
+                    acc[3] = fmaf(wa, t.w, acc[3]);
+                } else {
+                    acc[0] = fmaf(wa, __ldg(row), acc[0]);
+                }
+            }
+        }
+        if constexpr (V == 4) *reinterpret_cast<float4*>(dst + i * pitch) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        else dst[i * pitch] = acc[0];
     }
 }
 
@@ -440,8 +480,13 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     if (KX > 64) return RS_ERR_UNSUPPORTED;   // > 16x upscale along x
     // Two passes for upscales (dY larger than dX); the single-pass tiled
     // kernel for downscales, where it measures faster.
-    const bool two_pass = o.impl != RS_IMPL_TILED && KX <= 32 &&
-                          (int64_t)g.Ho * g.Wo >= (int64_t)g.H * g.W;
+    // The two passes use 32-bit offsets within a plane and index the y taps
+    // with at most 32 entries.
+    const bool two_pass = o.impl != RS_IMPL_TILED && KX <= 32 && p.yK <= 32 &&
+                          (int64_t)g.Ho * g.Wo >= (int64_t)g.H * g.W &&
+                          (int64_t)g.Ho * g.dst_pitch < (int64_t)INT32_MAX &&
+                          (int64_t)g.H * g.src_pitch < (int64_t)INT32_MAX &&
+                          (int64_t)g.Ho * g.W * g.C < (int64_t)INT32_MAX;
     AdjCfg cfg;
     if (!two_pass) {
         bool ok = false;
@@ -473,7 +518,13 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     if (two_pass) {
         float* T = reinterpret_cast<float*>(ws + p.off_t);
         const int rpt = 8;
-        const unsigned gx = (unsigned)(((int64_t)g.W * g.C + kAdjThreads - 1) / kAdjThreads);
+        const int WC = g.W * g.C;
+        const unsigned gx = (unsigned)((WC + kAdjThreads - 1) / kAdjThreads);
+        // 16-byte y-pass rows: whole float4s in every T and dX row.
+        const bool v4 = WC % 4 == 0 && g.src_pitch % 4 == 0 && reinterpret_cast<uintptr_t>(dX) % 16 == 0 &&
+                        (g.planes == 1 || (g.sp.n_stride % 4 == 0 && g.sp.c_stride % 4 == 0));
+        const int V = v4 ? 4 : 1;
+        const unsigned gy = (unsigned)((WC / V + kAdjThreads - 1) / kAdjThreads);
         for (int p0 = 0; p0 < g.planes; p0 += p.group_planes) {
             const int np = std::min(p.group_planes, g.planes - p0);
             dim3 gxg(gx, (unsigned)((g.Ho + rpt - 1) / rpt), (unsigned)np);
@@ -482,8 +533,19 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
             else if (KX <= 16) k_adj_x<16><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
             else k_adj_x<32><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-            dim3 gyg(gx, (unsigned)((g.H + rpt - 1) / rpt), (unsigned)np);
-            k_adj_y<<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+            dim3 gyg(gy, (unsigned)((g.H + rpt - 1) / rpt), (unsigned)np);
+            const int KY = p.yK;
+            if (v4) {
+                if (KY <= 4) k_adj_y<4, 4><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else if (KY <= 8) k_adj_y<8, 4><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else if (KY <= 16) k_adj_y<16, 4><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else k_adj_y<32, 4><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+            } else {
+                if (KY <= 4) k_adj_y<4, 1><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else if (KY <= 8) k_adj_y<8, 1><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else if (KY <= 16) k_adj_y<16, 1><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+                else k_adj_y<32, 1><<<gyg, kAdjThreads, 0, st>>>(g, T, dX, tb, p0, rpt);
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
         }
         return RS_OK;
