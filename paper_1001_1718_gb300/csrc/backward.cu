@@ -478,12 +478,10 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     }
     const int KX = p.xK;
     if (KX > 64) return RS_ERR_UNSUPPORTED;   // > 16x upscale along x
-    // Two passes for upscales (dY larger than dX); the single-pass tiled
-    // kernel for downscales, where it measures faster.
-    // The two passes use 32-bit offsets within a plane and index the y taps
-    // with at most 32 entries.
+    // Two passes by default (they measure faster than the tiled kernel at
+    // both x2 and x0.5); they use 32-bit offsets within a plane and index
+    // the y taps with at most 32 entries.
     const bool two_pass = o.impl != RS_IMPL_TILED && KX <= 32 && p.yK <= 32 &&
-                          (int64_t)g.Ho * g.Wo >= (int64_t)g.H * g.W &&
                           (int64_t)g.Ho * g.dst_pitch < (int64_t)INT32_MAX &&
                           (int64_t)g.H * g.src_pitch < (int64_t)INT32_MAX &&
                           (int64_t)g.Ho * g.W * g.C < (int64_t)INT32_MAX;
