@@ -64,8 +64,8 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
  * AUTO   = the tuned (or default) kernel for the problem: GATHER for
  *          RS_NEAREST; WINDOW for bilinear / bicubic when its footprint fits
  *          in shared memory, else STREAM, else TILED.
- * WINDOW = bilinear / bicubic: each thread owns 4 output elements of a
- *          1024-element strip for a whole band of rows and keeps the
+ * WINDOW = bilinear / bicubic: each thread owns 4 output elements (strided
+ *          by 256) of a 1024-element strip for a whole band of rows and keeps the
  *          horizontally interpolated source rows its taps need in registers,
  *          so each output row is blended without touching shared memory;
  *          source rows are staged in chunks of tile_h rows (double
@@ -79,10 +79,16 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
  *          block slot (sets the band height).
  * TILED  = one block per output tile of tile_w elements x tile_h rows with
  *          `threads` threads; the footprint and halo are staged per tile.
- * GATHER = RS_NEAREST only (AUTO's choice for it): a bit-exact gather, each
- *          thread copying 16 bytes of a strip of tile_w output elements over
- *          tile_h consecutive output rows, reusing a gathered row for the
- *          next output row when both map to the same source row.
+ * GATHER = RS_NEAREST only (AUTO's choice for it): a bit-exact gather.
+ *          tile_w = 256 x 16 bytes (default) with upsampled columns and
+ *          16-byte-aligned source rows: a block walks the distinct source
+ *          rows of a band of tile_h output rows (default: 16..256 rows, about
+ *          two to three blocks per SM), staging each
+ *          one's bytes under its 4096-byte strip in shared memory three
+ *          rows ahead, and writes every output row that maps to it.
+ *          Otherwise each thread copies 16 bytes of a strip of tile_w output
+ *          elements over tile_h consecutive output rows, reusing a gathered
+ *          row for the next output row when both map to the same source row.
  * PLAIN  = one thread per output pixel reading its taps from global memory,
  *          thread blocks of tile_w x tile_h threads (default 32 x 4): the
  *          paper's kernel (Sec. III.A, Eq. 6), kept as the comparison row. */

@@ -122,8 +122,9 @@ static bool make_choice(const Geom& g, int method, int dtype, const void* src, c
 static bool default_choice(const Geom& g, int method, int dtype, const void* src, KernelChoice& k)
 {
     if (method == RS_NEAREST) {
-        // 64 threads per output row of the strip (1 KB), 16 rows per thread
-        const Tuned t{RS_IMPL_GATHER, 64 * (16 / (int)dtype_size(dtype)), 16, 256, 0};
+        // Strips of 4096 bytes (256 threads across): the staged-rows kernel
+        // where its conditions hold, else the per-thread gather.
+        const Tuned t{RS_IMPL_GATHER, 256 * (16 / (int)dtype_size(dtype)), nearest_default_rows(g, dtype), 256, 0};
         if (make_choice(g, method, dtype, src, t, k)) return true;
     }
     // Register window for vertical upscales of large outputs (at a
@@ -154,7 +155,8 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
     const bool explicit_shape = o.tile_w || o.tile_h || o.threads || o.waves;
     if (o.impl == RS_IMPL_GATHER) {
         const int ev = 16 / (int)dtype_size(dtype);
-        const Tuned t{RS_IMPL_GATHER, o.tile_w ? o.tile_w : 64 * ev, o.tile_h ? o.tile_h : 16, 256, 0};
+        const Tuned t{RS_IMPL_GATHER, o.tile_w ? o.tile_w : 256 * ev, o.tile_h ? o.tile_h : nearest_default_rows(g, dtype),
+                      256, 0};
         if (method != RS_NEAREST) return RS_ERR_INVALID_ARG;
         return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
     }
@@ -268,7 +270,7 @@ rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_
     if (method == RS_NEAREST) {
         const int ev = 16 / (int)dtype_size(dtype);
         for (int nv : {8, 16, 32, 64, 128, 256})
-            for (int rows : {1, 2, 4, 8, 16}) cands.push_back(Tuned{RS_IMPL_GATHER, nv * ev, rows, 256, 0});
+            for (int rows : {1, 2, 4, 8, 16, 32, 64, 128, 256}) cands.push_back(Tuned{RS_IMPL_GATHER, nv * ev, rows, 256, 0});
     }
     KernelChoice def;
     if (!default_choice(g, method, dtype, src, def)) return RS_ERR_UNSUPPORTED;

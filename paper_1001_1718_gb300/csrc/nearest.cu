@@ -14,6 +14,7 @@
 // without reloading. Gathers go through the read-only data cache; stores
 // are one 16-byte store per thread and row (scalar at unaligned edges).
 #include <algorithm>
+#include <climits>
 
 #include "capi_internal.h"
 #include "rs_common.cuh"
@@ -151,6 +152,152 @@ k_nearest(const Geom g, const T* __restrict__ src, T* __restrict__ dst, int tile
 }
 
 // ---------------------------------------------------------------------------
+// Staged rows (upsampled columns, 16-byte source rows, 4-byte output rows).
+//
+// A block owns a strip of 4096 output bytes and a band of output rows and
+// walks the band's distinct source rows ("positions") in order. Each
+// position's source bytes under the strip are copied into a ring of
+// kNnSlots shared-memory rows with 16-byte cp.async copies, kNnSlots - 1
+// positions ahead, so DRAM latency is hidden behind the gathers of earlier
+// positions (one barrier per position). Thread t owns output words t,
+// t + 256, t + 512 and t + 768 of the strip: consecutive lanes read
+// neighbouring staged words (no bank conflicts) and each output word is one
+// byte permutation of two staged words, stored once per output row that
+// maps to the position.
+static constexpr int kNnSlots = 4;
+static constexpr int kNnStripBytes = 4096;
+
+template <int C, typename T>
+__global__ void __launch_bounds__(kNnThreads)
+k_nearest_rows(const Geom g, const T* __restrict__ src, T* __restrict__ dst, int band_rows, int span_units,
+               unsigned int* fault)
+{
+    constexpr int ES = (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char nsm[];
+    const int tid = threadIdx.x;
+    const int plane = blockIdx.z;
+    const unsigned char* s = reinterpret_cast<const unsigned char*>(src + g.sp.offset(plane));
+    unsigned char* d = reinterpret_cast<unsigned char*>(dst + g.dp.offset(plane));
+    const int64_t out_row_bytes = (int64_t)g.Wo * C * ES;
+    const int64_t b0 = (int64_t)blockIdx.x * kNnStripBytes;
+    const int nb = (int)min((int64_t)kNnStripBytes, out_row_bytes - b0);
+    const int yb = blockIdx.y * band_rows;
+    const int nrows = min(band_rows, g.Ho - yb);
+    unsigned char* ring = nsm;                                           // [kNnSlots][span_units * 16]
+    int* rowtab = reinterpret_cast<int*>(nsm + (size_t)kNnSlots * span_units * 16);   // [band_rows]
+    int* pos_r = rowtab + band_rows;                                     // [band_rows]
+    int* pos_i = pos_r + band_rows;                                      // [band_rows + 1]
+
+    // Source bytes under the strip, in whole aligned 16-byte units.
+    auto src_byte = [&](int64_t ob) -> int64_t {   // source byte of output byte ob of a row
+        const int64_t e = ob / ES;
+        const int j = (int)(e / C), c = (int)(e - (int64_t)j * C);
+        return ((int64_t)clampi(nearest_index(j, g.W, g.Wo, g.coord), g.W) * C + c) * ES + (ob - e * ES);
+    };
+    // (whole source pixels: a strip may start or end inside an output pixel)
+    const int j_first = (int)(b0 / ES / C), j_last = (int)((b0 + nb - 1) / ES / C);
+    const int64_t unit0 = ((int64_t)clampi(nearest_index(j_first, g.W, g.Wo, g.coord), g.W) * C * ES) >> 4;
+    const int64_t src_end = ((int64_t)clampi(nearest_index(j_last, g.W, g.Wo, g.coord), g.W) + 1) * C * ES;
+    const int units = (int)(((src_end + 15) >> 4) - unit0);
+    if (units > span_units || band_rows > kNnMaxRows) {   // uniform; the host sizes both
+        if (tid == 0) report_fault(fault, FAULT_TILE_SRC_SPAN);
+        return;
+    }
+
+    // Output word q of this thread: bytes 4 (tid + 256 q) .. +3 of the strip.
+    int wa[4], wb[4];
+    uint32_t sel[4];
+    bool fit = true;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int wo = 4 * (tid + kNnThreads * q);
+        int rel[4];
+        #pragma unroll
+        for (int i = 0; i < 4; ++i)
+            rel[i] = (int)(src_byte(b0 + min(wo + i, nb - 1)) - unit0 * 16);
+        const int lo = min(min(rel[0], rel[1]), min(rel[2], rel[3])) & ~3;
+        const int hi = max(max(rel[0], rel[1]), max(rel[2], rel[3])) - lo;
+        fit = fit && hi < 8;
+        uint32_t m = 0;
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) m |= (uint32_t)((rel[i] - lo) & 7) << (4 * i);
+        sel[q] = m;
+        wa[q] = lo >> 2;
+        wb[q] = hi >= 4 ? (lo >> 2) + 1 : (lo >> 2);
+    }
+    if (!fit) {   // excluded by the host (columns are upsampled)
+        report_fault(fault, FAULT_TILE_SRC_SPAN);
+    }
+
+    // Source row of every output row of the band, then the positions: runs
+    // of equal source rows. Rows never decrease; with rows upsampled every
+    // source row between the first and the last is hit, with rows
+    // downsampled every output row has its own.
+    for (int i = tid; i < nrows; i += kNnThreads) rowtab[i] = clampi(nearest_index(yb + i, g.H, g.Ho, g.coord), g.H);
+    __syncthreads();
+    const bool rows_up = g.Ho >= g.H;
+    const int npos = rows_up ? rowtab[nrows - 1] - rowtab[0] + 1 : nrows;
+    if (npos > band_rows) {   // uniform; impossible by the argument above
+        if (tid == 0) report_fault(fault, FAULT_TILE_SRC_SPAN);
+        return;
+    }
+    for (int i = tid; i < nrows; i += kNnThreads) {
+        if (i == 0 || rowtab[i] != rowtab[i - 1]) {
+            const int p = rows_up ? rowtab[i] - rowtab[0] : i;
+            pos_r[p] = rowtab[i];
+            pos_i[p] = i;
+        }
+    }
+    if (tid == 0) pos_i[npos] = nrows;
+    __syncthreads();
+
+    // One commit group per position (empty past the last one).
+    auto issue = [&](int p) {
+        if (p < npos) {
+            const unsigned char* row = s + (int64_t)pos_r[p] * g.src_pitch * ES + unit0 * 16;
+            unsigned char* slot = ring + (size_t)(p % kNnSlots) * span_units * 16;
+            for (int u = tid; u < units; u += kNnThreads) {
+                const unsigned sdst = (unsigned)__cvta_generic_to_shared(slot + u * 16);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(row + u * 16) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    #pragma unroll
+    for (int p = 0; p < kNnSlots - 1; ++p) issue(p);
+
+    unsigned char* dband = d + (int64_t)yb * g.dst_pitch * ES + b0;
+    const int pitch_b = (int)(g.dst_pitch * ES);
+    for (int p = 0; p < npos; ++p) {
+        // This thread's copies of position p are done (later groups may
+        // still be in flight); the barrier makes every thread's copies
+        // visible and ends all reads of the slot that position
+        // p + kNnSlots - 1 reuses.
+        asm volatile("cp.async.wait_group %0;" ::"n"(kNnSlots - 2) : "memory");
+        __syncthreads();
+        issue(p + kNnSlots - 1);
+        const uint32_t* W = reinterpret_cast<const uint32_t*>(ring + (size_t)(p % kNnSlots) * span_units * 16);
+        uint32_t v[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __byte_perm(W[wa[q]], W[wb[q]], sel[q]);
+        const int i_end = pos_i[p + 1];
+        for (int i = pos_i[p]; i < i_end; ++i) {
+            unsigned char* out = dband + i * pitch_b;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int wo = 4 * (tid + kNnThreads * q);
+                if (wo + 4 <= nb) {
+                    *reinterpret_cast<uint32_t*>(out + wo) = v[q];
+                } else if (wo < nb) {
+                    for (int k = 0; k < nb - wo; ++k) out[wo + k] = (unsigned char)(v[q] >> (8 * k));
+                }
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 
 template <int C, typename T>
 static void* nn_func(bool words)
@@ -190,6 +337,71 @@ static bool nn_words(const Geom& g, int dtype, const void* src)
     return true;
 }
 
+template <int C, typename T>
+static void* nn_rows_func_c() { return reinterpret_cast<void*>(&k_nearest_rows<C, T>); }
+
+template <typename T>
+static void* nn_rows_func(int C)
+{
+    switch (C) {
+    case 1: return nn_rows_func_c<1, T>();
+    case 2: return nn_rows_func_c<2, T>();
+    case 3: return nn_rows_func_c<3, T>();
+    default: return nn_rows_func_c<4, T>();
+    }
+}
+
+static void* nn_rows_kernel(int dtype, int C)
+{
+    switch (dtype) {
+    case DT_U8: return nn_rows_func<uint8_t>(C);
+    case DT_F16: return nn_rows_func<__half>(C);
+    case DT_BF16: return nn_rows_func<__nv_bfloat16>(C);
+    default: return nn_rows_func<float>(C);
+    }
+}
+
+// The staged-rows kernel: strips of 4096 output bytes (tile_w = 256 x 16 /
+// element size), upsampled columns, source rows of whole aligned 16-byte
+// units, output rows of whole aligned words, and 32-bit row offsets within
+// a band.
+static bool nn_rows_ok(const Geom& g, int dtype, const void* src, const void* dst, int tile_w, int band)
+{
+    const int64_t es = (int64_t)dtype_size(dtype);
+    if (tile_w * es != kNnStripBytes || g.Wo < g.W || band < 1 || band > kNnMaxRows) return false;
+    if (reinterpret_cast<uintptr_t>(src) % 16 || (g.src_pitch * es) % 16 || ((int64_t)g.W * g.C * es) % 16) return false;
+    if (g.planes > 1 && ((g.sp.n_stride * es) % 16 || (g.sp.c_stride * es) % 16)) return false;
+    if (reinterpret_cast<uintptr_t>(dst) % 4 || (g.dst_pitch * es) % 4) return false;
+    if (g.planes > 1 && ((g.dp.n_stride * es) % 4 || (g.dp.c_stride * es) % 4)) return false;
+    return (int64_t)band * g.dst_pitch * es < (int64_t)INT32_MAX;
+}
+
+// Upper bound of the 16-byte units a strip of 4096 output bytes reads from
+// one source row: its source bytes span at most (4096 / C / es / scale + 1)
+// pixels.
+static int nn_rows_units(const Geom& g, int dtype)
+{
+    const int64_t es = (int64_t)dtype_size(dtype);
+    const int64_t px_out = kNnStripBytes / (g.C * es) + 2;
+    const int64_t px_src = (px_out * g.W + g.Wo - 1) / g.Wo + 2;
+    return (int)((px_src * g.C * es + 15) / 16 + 2);
+}
+
+// Default band height of the gather: for the staged-rows kernel, bands that
+// leave about two to three blocks per SM (long bands keep each block's
+// prefetch ring busy; measured best at 128 rows for an RGB 8192 output),
+// between 16 and 256 rows; 32 rows per thread for the per-thread kernel.
+int nearest_default_rows(const Geom& g, int dtype)
+{
+    if (g.Wo < g.W) return 32;
+    const int64_t es = (int64_t)dtype_size(dtype);
+    const int64_t strips = ((int64_t)g.Wo * g.C * es + kNnStripBytes - 1) / kNnStripBytes;
+    const double target = (double)strips * g.Ho * g.planes / (2.5 * num_sms());
+    int band = 16;
+    while (band < 256 && 2.0 * band <= target) band *= 2;
+    return band;
+}
+
 bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread)
 {
     const int EV = 16 / (int)dtype_size(dtype);
@@ -204,6 +416,24 @@ bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread)
 cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst, int tile_w, int rows_per_thread,
                            cudaStream_t st)
 {
+    if (nn_rows_ok(g, dtype, src, dst, tile_w, rows_per_thread)) {
+        const int band = rows_per_thread;
+        const int span_units = nn_rows_units(g, dtype);
+        const size_t smem = (size_t)kNnSlots * span_units * 16 + sizeof(int) * (3 * (size_t)band + 1);
+        if (smem <= max_smem_per_block()) {
+            void* func = nn_rows_kernel(dtype, g.C);
+            cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int64_t es = (int64_t)dtype_size(dtype);
+            dim3 grid((unsigned)(((int64_t)g.Wo * g.C * es + kNnStripBytes - 1) / kNnStripBytes),
+                      (unsigned)((g.Ho + band - 1) / band), (unsigned)g.planes);
+            unsigned int* fw = fault_word();
+            int span = span_units;
+            void* args[] = {const_cast<Geom*>(&g), const_cast<void**>(&src), &dst, const_cast<int*>(&band), &span, &fw};
+            e = cudaLaunchKernel(func, grid, dim3(kNnThreads), args, smem, st);
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
+    }
     const int EV = 16 / (int)dtype_size(dtype);
     const int vpp = kNnThreads / (tile_w / EV);
     const int band = vpp * rows_per_thread;

@@ -103,6 +103,7 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
 cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c,
                         cudaStream_t st);
 bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread);
+int nearest_default_rows(const Geom& g, int dtype);
 cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst, int tile_w, int rows_per_thread,
                            cudaStream_t st);
 cudaError_t launch_plain(const Geom& g, int method, int dtype, const void* src, void* dst,

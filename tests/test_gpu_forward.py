@@ -253,3 +253,25 @@ def test_window_kernel_configs(rs, oracle, cfg, dtype):
         check(y, oracle.resize(x64, Ho, Wo, method, coord), dtype, method, np.abs(x64).max(),
               f"window {cfg} {dtype} {H}x{W}x{C}->{Ho}x{Wo}")
     assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+@pytest.mark.parametrize("band", [None, 1, 7, 100])
+def test_gather_staged_rows(rs, oracle, dtype, band):
+    """The staged-rows nearest kernel (4096-byte strips, source rows of whole
+    16-byte units, upsampled columns): several strips with a ragged last one,
+    strips that start inside an output pixel, rows up- and downsampled, both
+    coordinate maps, bit-exact against the oracle and the tiled kernel."""
+    es = {"u8": 1, "f16": 2, "f32": 4}[dtype]
+    tile = (4096 // es, band) if band else None
+    for k, (H, W, C, Ho, Wo, coord) in enumerate([(64, 1024, 3, 150, 2048, 0), (33, 512, 1, 20, 3001, 1),
+                                                   (40, 256, 4, 97, 700, 0), (7, 96, 2, 300, 129, 1),
+                                                   (120, 48, 3, 37, 4097, 0)]):
+        if (W * C * es) % 16:
+            W += (16 // np.gcd(16, C * es)) - W % (16 // np.gcd(16, C * es))
+        t, x64 = _src(900 + k, (H, W, C), dtype)
+        y = rs.resize(t.cuda(), (Ho, Wo), "nearest", coord=CNAME[coord], impl="gather", tile=tile)
+        torch.cuda.synchronize()
+        check(y, oracle.resize(x64, Ho, Wo, NN, coord), dtype, NN, 1.0, f"staged {dtype} {band} {H}x{W}x{C}->{Ho}x{Wo}")
+        assert torch.equal(y, rs.resize(t.cuda(), (Ho, Wo), "nearest", coord=CNAME[coord], impl="tiled"))
+    assert rs.debug_fault() == 0
