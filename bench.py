@@ -384,12 +384,27 @@ def run_e2e(torch, rs, img, outs, dev, stream, steps, warmup):
     names = [n for n, _, _ in HEADLINE_OPS]
     meth = {n: m for n, m, _ in HEADLINE_OPS}
 
+    # Each output's device-to-host copy runs on a copy stream as soon as its
+    # resize is done, overlapping the next resizes and the next step's
+    # host-to-device copy; a resize waits until the previous copy of its
+    # output buffer has finished.
+    copy_stream = torch.cuda.Stream(dev)
+    ev_k = {n: torch.cuda.Event() for n in names}
+    ev_c = {n: torch.cuda.Event() for n in names}
+    for n in names:
+        ev_c[n].record(copy_stream)
+
     def step():
         dev_in.copy_(host_in, non_blocking=True)
         for n in names:
             y = outs[n][0]
+            stream.wait_event(ev_c[n])
             rs.resize(dev_in, y.shape[:2], meth[n], out=y)
-            host_out[n].copy_(y, non_blocking=True)
+            ev_k[n].record(stream)
+            copy_stream.wait_event(ev_k[n])
+            with torch.cuda.stream(copy_stream):
+                host_out[n].copy_(y, non_blocking=True)
+            ev_c[n].record(copy_stream)
 
     for _ in range(warmup):
         step()
@@ -398,6 +413,8 @@ def run_e2e(torch, rs, img, outs, dev, stream, steps, warmup):
     a.record(stream)
     for _ in range(steps):
         step()
+    for n in names:   # the timed region ends when every copy has landed
+        stream.wait_event(ev_c[n])
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
