@@ -99,7 +99,7 @@ k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict_
         pc.raw_row = im.raw_row;
         pc.raw_off = im.raw_off;
         pc.smem = 0;
-        poly_body<KT, C, T>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), pc,
+        poly_body<KT, C, T, 2>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), pc,
                             (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
         __syncthreads();   // the next item reuses shared memory
     }
@@ -212,7 +212,8 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
             if (!ch) continue;
             PolyCfg pc{};
             pc.chunk = ch;
-            if (!poly_config(g, x.method, dtype, x.src, pc) || pc.smem > 100 * 1024) continue;
+            // batch items always stage shifted blocks (one kernel per class)
+            if (!poly_config(g, x.method, dtype, x.src, pc, true) || pc.smem > 100 * 1024) continue;
             im.kind = 1;
             im.chunk = pc.chunk;
             im.band_h = std::min(pc.band_cap, sh.band);

@@ -7,28 +7,37 @@
 #include "capi_internal.h"
 #include "poly_body.cuh"
 
+// This file is compiled twice: as poly.cu (POLY_MODE 1, aligned staging,
+// plus the host configuration and launch) and through poly_shifted.cu
+// (POLY_MODE 2, shifted staging), so the two sets of kernels build in
+// parallel.
+#ifndef POLY_MODE
+#define POLY_MODE 1
+#endif
+
 namespace rs {
 
-template <int KT, int C, typename T>
+template <int KT, int C, typename T, int MODE>
 __global__ void __launch_bounds__(kPolyThreads, 3)
 k_poly(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const PolyCfg cfg, unsigned int* fault)
 {
     extern __shared__ __align__(16) float sm[];
     const int plane = blockIdx.z;
-    poly_body<KT, C, T>(g, src + g.sp.offset(plane), dst + g.dp.offset(plane), cfg, blockIdx.x, blockIdx.y, sm,
-                        fault);
+    poly_body<KT, C, T, MODE>(g, src + g.sp.offset(plane), dst + g.dp.offset(plane), cfg, blockIdx.x, blockIdx.y,
+                              sm, fault);
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 
+#if POLY_MODE == 1
 static int poly_span_bound(int k, int n, int m, int KT)
 {
     const int64_t num = (int64_t)(k - 1) * n;
     return (int)((num + m - 1) / m) + KT;
 }
 
-bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c)
+bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c, bool shifted_only)
 {
     if (method != M_BILINEAR && method != M_BICUBIC) return false;
     const int KT = method_taps(method);
@@ -36,8 +45,9 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
     if (c.chunk < KT) return false;
     const uintptr_t basep = reinterpret_cast<uintptr_t>(src);
     const bool planar = g.sp.cp > 1 || g.planes > 1;
+    // 16-byte-aligned rows of whole units (1), else the shifted copies (2).
     c.vec = (basep % 16 == 0) && ((g.src_pitch * es) % 16 == 0) && (((int64_t)g.W * g.C * es) % 16 == 0) &&
-            (!planar || ((g.sp.n_stride * es) % 16 == 0 && (g.sp.c_stride * es) % 16 == 0)) ? 1 : 0;
+            (!planar || ((g.sp.n_stride * es) % 16 == 0 && (g.sp.c_stride * es) % 16 == 0)) && !shifted_only ? 1 : 2;
     const int EPU = c.vec ? 16 / es : 1;
     const int kpx = (kPolyElems + g.C - 1) / g.C + 1;
     const int span_px = poly_span_bound(kpx, g.W, g.Wo, KT);
@@ -48,44 +58,62 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
     const size_t tables = sizeof(float) * (2 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KT) +
                           sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);
     c.raw_off = (int)((tables + 15) & ~(size_t)15);
-    c.raw_row = c.vec ? (c.swe_max / EPU + 2) * 16 : 0;
+    c.raw_row = c.vec ? (c.swe_max / EPU + (c.vec == 2 ? 3 : 2)) * 16 : 0;
     c.smem = (size_t)c.raw_off + 3 * (size_t)c.chunk * c.raw_row;
     return c.smem <= max_smem_per_block();
 }
 
+#endif
+
 template <int KT, int C, typename T>
-static void* poly_func() { return reinterpret_cast<void*>(&k_poly<KT, C, T>); }
+static void* poly_func(int) { return reinterpret_cast<void*>(&k_poly<KT, C, T, POLY_MODE>); }
 
 template <int KT, typename T>
-static void* poly_func_c(int C)
+static void* poly_func_c(int C, int mode)
 {
     switch (C) {
-    case 1: return poly_func<KT, 1, T>();
-    case 2: return poly_func<KT, 2, T>();
-    case 3: return poly_func<KT, 3, T>();
-    default: return poly_func<KT, 4, T>();
+    case 1: return poly_func<KT, 1, T>(mode);
+    case 2: return poly_func<KT, 2, T>(mode);
+    case 3: return poly_func<KT, 3, T>(mode);
+    default: return poly_func<KT, 4, T>(mode);
     }
 }
 
 template <typename T>
-static void* poly_func_m(int method, int C)
+static void* poly_func_m(int method, int C, int mode)
 {
-    return method == M_BILINEAR ? poly_func_c<2, T>(C) : poly_func_c<4, T>(C);
+    return method == M_BILINEAR ? poly_func_c<2, T>(C, mode) : poly_func_c<4, T>(C, mode);
 }
 
-static void* poly_kernel(int method, int dtype, int C)
+#if POLY_MODE == 1
+void* poly_kernel_shifted(int method, int dtype, int C);   // poly_shifted.cu
+static void* poly_kernel(int method, int dtype, int C, int mode)
 {
+    if (mode == 2) return poly_kernel_shifted(method, dtype, C);
     switch (dtype) {
-    case DT_U8: return poly_func_m<uint8_t>(method, C);
-    case DT_F16: return poly_func_m<__half>(method, C);
-    case DT_BF16: return poly_func_m<__nv_bfloat16>(method, C);
-    default: return poly_func_m<float>(method, C);
+    case DT_U8: return poly_func_m<uint8_t>(method, C, mode);
+    case DT_F16: return poly_func_m<__half>(method, C, mode);
+    case DT_BF16: return poly_func_m<__nv_bfloat16>(method, C, mode);
+    default: return poly_func_m<float>(method, C, mode);
     }
 }
+#else
+void* poly_kernel_shifted(int method, int dtype, int C)
+{
+    switch (dtype) {
+    case DT_U8: return poly_func_m<uint8_t>(method, C, 2);
+    case DT_F16: return poly_func_m<__half>(method, C, 2);
+    case DT_BF16: return poly_func_m<__nv_bfloat16>(method, C, 2);
+    default: return poly_func_m<float>(method, C, 2);
+    }
+}
+#endif
+
+#if POLY_MODE == 1
 
 cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c, cudaStream_t st)
 {
-    void* func = poly_kernel(method, dtype, g.C);
+    void* func = poly_kernel(method, dtype, g.C, c.vec);
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     const int64_t strips = ((int64_t)g.Wo * g.C + kPolyElems - 1) / kPolyElems;
@@ -105,5 +133,7 @@ cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, v
     e = cudaLaunchKernel(func, grid, dim3(kPolyThreads), args, c.smem, st);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+#endif
 
 }  // namespace rs

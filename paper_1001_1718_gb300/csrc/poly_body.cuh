@@ -111,13 +111,19 @@ __device__ __forceinline__ void poly_unpack16(const uint4& u, float* dst)
     }
 }
 
+__device__ __forceinline__ float raw_to_float(uint8_t v) { return (float)v; }
+__device__ __forceinline__ float raw_to_float(__half v) { return __half2float(v); }
+__device__ __forceinline__ float raw_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float raw_to_float(float v) { return v; }
+
 // The work of one block: strip bx (1024 output elements) and band by of
 // one plane (s, d already point at the plane). Used by the single-image
 // kernel and by the persistent batched kernel.
-template <int KT, int C, typename T>
+template <int KT, int C, typename T, int MODE>
 __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s, T* __restrict__ d,
                                           const PolyCfg& cfg, int bx, int by, float* sm, unsigned int* fault)
 {
+    static_assert(MODE == 1 || MODE == 2, "staging mode: 1 aligned units, 2 shifted blocks");
     const int tid = threadIdx.x;
 
     const int64_t WoC = (int64_t)g.Wo * C;
@@ -134,7 +140,7 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     const int j_first = (int)(e0 / C), j_last = (int)((e0 + nE - 1) / C);
     const int px_lo = first_tap<KT>(j_first, g.W, g.Wo, g.coord);
     const int px_hi = first_tap<KT>(j_last, g.W, g.Wo, g.coord) + KT - 1;
-    const int EPU = cfg.vec ? 16 / (int)sizeof(T) : 1;
+    constexpr int EPU = 16 / (int)sizeof(T);
     const int in_lo = max(px_lo, 0) * C, in_hi = (min(px_hi, g.W - 1) + 1) * C;
     const int a0 = (in_lo / EPU) * EPU;
     const int units = (in_hi - a0 + EPU - 1) / EPU;
@@ -154,7 +160,12 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     int* NC = RF + cfg.band_cap;                           // [pos_cap] rows per position
     // Raw 16-byte load units of the next two chunks (vector path): [3][R][raw_row].
     unsigned char* RAW = reinterpret_cast<unsigned char*>(sm) + cfg.raw_off;
-    if (cfg.vec && units * 16 > cfg.raw_row) {   // uniform; the host sizes raw rows
+    // MODE 1: 16-byte-aligned rows, each unit copied and converted by one
+    // thread; MODE 2 (shifted): rows at any element alignment, copied as the
+    // aligned 16-byte blocks around them (units + 1 per row) and realigned
+    // when converted.
+    constexpr bool shifted = MODE == 2;
+    if (cfg.vec != MODE || (units + (shifted ? 2 : 0)) * 16 > cfg.raw_row) {   // uniform; the host sizes raw rows
         if (tid == 0) report_fault(fault, FAULT_TILE_SRC_SPAN);
         return;
     }
@@ -236,33 +247,68 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
         }
         if (lpad + rpad) pads(r0, nn, dstb);
     };
-    // Element path (rows not 16-byte aligned): synchronous staging.
-    auto stage_sync = [&](int r0, int nn, float* dstb) {
-        const int total = nn * units;
-        for (int b0 = 0; b0 < total; b0 += 4 * kPolyThreads) {
-            float v[4];
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int u = b0 + tid + i * kPolyThreads;
-                if (u < total) {
-                    int k, w;
-                    split(u, k, w);
-                    v[i] = Store<T>::load(row_ptr(r0 + k) + a0 + w);
-                }
+    // Shifted path. Row k of a chunk starts its raw copy at the aligned
+    // block A below its first staged byte Rb = &row[a0] (phase Rb - A < 16)
+    // and copies units + 1 blocks. A block not wholly inside the plane (the
+    // first row's head, the last row's tail) is filled element by element
+    // instead, only with the staged elements it holds.
+    const uintptr_t plane_lo = reinterpret_cast<uintptr_t>(s);
+    const uintptr_t plane_hi = reinterpret_cast<uintptr_t>(s + (int64_t)(g.H - 1) * g.src_pitch + (int64_t)g.W * C);
+    const uint32_t umul1 = 0xFFFFFFFFu / (uint32_t)(units + 1) + 1u;
+    auto issue_shifted = [&](int r0, int nn, int slot) {
+        unsigned char* rb = RAW + (size_t)slot * R * cfg.raw_row;
+        const int per = units + 1;
+        for (int u = tid; u < nn * per; u += kPolyThreads) {
+            const int k = (int)__umulhi((uint32_t)u, umul1), w = u - k * per;
+            const uintptr_t rb0 = reinterpret_cast<uintptr_t>(row_ptr(r0 + k) + a0);
+            const uintptr_t blk = (rb0 & ~(uintptr_t)15) + 16 * (uintptr_t)w;
+            unsigned char* dsts = rb + k * cfg.raw_row + w * 16;
+            if (blk >= plane_lo && blk + 16 <= plane_hi) {
+                const unsigned sdst = (unsigned)__cvta_generic_to_shared(dsts);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst),
+                             "l"(reinterpret_cast<const void*>(blk)) : "memory");
+            } else {
+                const int phase = (int)(rb0 & 15);
+                // staged elements a0 + e with byte offset phase + e * es in [16 w, 16 w + 16)
+                const int es = (int)sizeof(T);
+                const int e_lo = max(0, (16 * w - phase + es - 1) / es);
+                const int e_hi = min(in_hi - a0, (16 * w + 16 - phase) / es);
+                const T* rowp = row_ptr(r0 + k) + a0;
+                for (int e = e_lo; e < e_hi; ++e)
+                    *reinterpret_cast<T*>(rb + k * cfg.raw_row + phase + e * es) = rowp[e];
             }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // Converts the staged groups of EPU elements of every row (any thread
+    // any group: a barrier precedes it), realigning by the row's phase.
+    auto convert_shifted = [&](int r0, int nn, int slot, float* dstb) {
+        const unsigned char* rb = RAW + (size_t)slot * R * cfg.raw_row;
+        const int valid = in_hi - a0;   // staged elements per row
+        for (int u = tid; u < nn * units; u += kPolyThreads) {
+            int k, w;
+            split(u, k, w);
+            const int phase = (int)(reinterpret_cast<uintptr_t>(row_ptr(r0 + k) + a0) & 15);
+            const uint32_t* W = reinterpret_cast<const uint32_t*>(rb + k * cfg.raw_row) + (phase >> 2) + 4 * w;
+            const int sh = 8 * (phase & 3);
+            uint32_t x[5];
             #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int u = b0 + tid + i * kPolyThreads;
-                if (u < total) {
-                    int k, w;
-                    split(u, k, w);
-                    dstb[k * cfg.swe_max + u0 + w] = v[i];
-                }
+            for (int q = 0; q < 5; ++q) x[q] = W[q];
+            uint4 v;
+            v.x = __funnelshift_r(x[0], x[1], sh);
+            v.y = __funnelshift_r(x[1], x[2], sh);
+            v.z = __funnelshift_r(x[2], x[3], sh);
+            v.w = __funnelshift_r(x[3], x[4], sh);
+            float* dp = dstb + k * cfg.swe_max + u0 + w * EPU;
+            if (w * EPU + EPU <= valid) {
+                poly_unpack16<T>(v, dp);
+            } else {   // the row's last group: positions past the image hold pads
+                const T* e = reinterpret_cast<const T*>(rb + k * cfg.raw_row + phase) + w * EPU;
+                for (int q = 0; w * EPU + q < valid; ++q) dp[q] = raw_to_float(e[q]);
             }
         }
         if (lpad + rpad) pads(r0, nn, dstb);
     };
-
     // Horizontal interpolation of a staged row at this thread's columns.
     auto hrow = [&](const float* Sr, float2& h01, float2& h23) {
         h01 = make_float2(0.0f, 0.0f);
@@ -296,16 +342,21 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     int cidx = 0;                                          // current chunk
     int chunk_lo = r_first;
     int nn = chunk_rows(0);
-    if (cfg.vec) {
+    if constexpr (shifted) {
+        issue_shifted(r_first, nn, 0);
+        issue_shifted(r_first + R, chunk_rows(1), 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        convert_shifted(r_first, nn, 0, SR);
+    } else {
         issue_async(r_first, nn, 0);
         issue_async(r_first + R, chunk_rows(1), 1);
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         convert(r_first, nn, 0, SR);
-    } else {
-        stage_sync(r_first, nn, SR);
     }
     __syncthreads();
-    if (cfg.vec) issue_async(r_first + 2 * R, chunk_rows(2), 2);
+    if constexpr (shifted) issue_shifted(r_first + 2 * R, chunk_rows(2), 2);
+    else issue_async(r_first + 2 * R, chunk_rows(2), 2);
     int half = 0;
 
     // Register window: h[p] holds source row (b + p) at position b.
@@ -381,14 +432,18 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
                     chunk_lo = r_first + cidx * R;
                     nn = chunk_rows(cidx);
                     float* dstb = SR + half * R * cfg.swe_max;
-                    if (cfg.vec) {
+                    if constexpr (shifted) {
+                        // every thread's copies must land before any converts
+                        asm volatile("cp.async.wait_group 1;" ::: "memory");
+                        __syncthreads();
+                        convert_shifted(chunk_lo, nn, cidx % 3, dstb);
+                    } else {
                         asm volatile("cp.async.wait_group 1;" ::: "memory");
                         convert(chunk_lo, nn, cidx % 3, dstb);
-                    } else {
-                        stage_sync(chunk_lo, nn, dstb);
                     }
                     __syncthreads();
-                    if (cfg.vec) issue_async(r_first + (cidx + 2) * R, chunk_rows(cidx + 2), (cidx + 2) % 3);
+                    if constexpr (shifted) issue_shifted(r_first + (cidx + 2) * R, chunk_rows(cidx + 2), (cidx + 2) % 3);
+                    else issue_async(r_first + (cidx + 2) * R, chunk_rows(cidx + 2), (cidx + 2) % 3);
                 }
                 // the newest row goes into slot (u + KT - 1) % KT
                 const int ns = (u + KT - 1) % KT;

@@ -70,7 +70,8 @@ struct StreamCfg {
 // Configuration of the register-window kernel (bilinear / bicubic): strips
 // of 1024 output elements, bands of band_h output rows (0 = from occupancy
 // and `waves`), source rows staged in chunks of `chunk` rows (double
-// buffered) of swe_max elements; vec = 16-byte loads.
+// buffered) of swe_max elements; vec = staging mode (1: aligned 16-byte
+// units, 2: shifted aligned blocks around rows of any alignment).
 struct PolyCfg {
     int chunk, band_h, waves, swe_max, band_cap, pos_cap, vec;
     int raw_row, raw_off;   // vector path: bytes per raw staged row, byte offset of the raw ring
@@ -99,7 +100,7 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
 StreamCfg stream_default(const Geom& g, int method, int dtype, const void* src);
 cudaError_t launch_stream(const Geom& g, int method, int dtype, const void* src, void* dst, StreamCfg c,
                           cudaStream_t st);
-bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c);
+bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c, bool shifted_only = false);
 cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c,
                         cudaStream_t st);
 bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread);
