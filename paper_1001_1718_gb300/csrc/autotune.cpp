@@ -127,14 +127,16 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
         const Tuned t{RS_IMPL_GATHER, 256 * (16 / (int)dtype_size(dtype)), nearest_default_rows(g, dtype), 256, 0};
         if (make_choice(g, method, dtype, src, t, k)) return true;
     }
-    // Register window for vertical upscales of large outputs (at a
-    // downscale a chunk covers few output rows; a small output has too few
-    // strips and bands to fill the GPU), 8-row chunks within ~100 KB.
+    // Register window for large outputs (a small output has too few strips
+    // and bands to fill the GPU) of vertical upscales, and of uint8
+    // downscales (measured faster than the streaming kernel there, slower
+    // for FP32): 8-row chunks when they leave room for three blocks per SM,
+    // else 4-row chunks, within ~100 KB.
     const int64_t out_elems = (int64_t)g.Ho * g.Wo * g.C * g.planes;
-    if (g.Ho >= g.H && out_elems >= (int64_t)1 << 22) {
+    if ((g.Ho >= g.H || dtype == DT_U8) && out_elems >= (int64_t)1 << 22) {
         for (int ch : {8, 4}) {
             const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
-            if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= 100 * 1024) return true;
+            if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= (ch == 8 ? 72 : 100) * 1024) return true;
         }
     }
     StreamCfg sc = stream_default(g, method, dtype, src);
