@@ -52,10 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="tune tile shapes before timing")
     ap.add_argument("--ops-only", nargs="?", const="headline", default=None,
-                    choices=["headline", "backward", "batch"],
+                    choices=["headline", "nchw", "backward", "batch"],
                     help="profiling driver: run warmup + steps of the three headline resizes (headline), "
-                         "of the NCHW FP32 backward x2 / x0.5 (backward) or of the 256-image batch plan "
-                         "(batch), and exit")
+                         "of the NCHW FP32 forward or backward x2 / x0.5 (nchw, backward) or of the "
+                         "256-image batch plan (batch), and exit")
     return ap.parse_args()
 
 
@@ -252,10 +252,18 @@ def torch_index(a):
 
 
 def profile_ops(args, torch, rs, workloads, dev):
-    """Untimed launches for profiling under ncu: the NCHW FP32 backward
-    (bilinear / bicubic, x2 and x0.5 of 32x3x512x512) or the replayable plan
-    of the 256-image ragged batch."""
-    if args.ops_only == "backward":
+    """Untimed launches for profiling under ncu: the NCHW FP32 forward or
+    backward (bilinear / bicubic, x2 and x0.5 of 32x3x512x512) or the
+    replayable plan of the 256-image ragged batch."""
+    if args.ops_only == "nchw":
+        xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
+        ops = []
+        for method in ("bilinear", "bicubic"):
+            for s in (2.0, 0.5):
+                Ho = int(512 * s)
+                y = torch.empty((32, 3, Ho, Ho), dtype=torch.float32, device=dev)
+                ops.append(lambda y=y, m=method, Ho=Ho: rs.resize(xn, (Ho, Ho), m, layout="nchw", out=y))
+    elif args.ops_only == "backward":
         xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
         ops = []
         for method in ("bilinear", "bicubic"):
@@ -288,7 +296,7 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream(dev)
 
-    if args.ops_only in ("backward", "batch"):
+    if args.ops_only in ("nchw", "backward", "batch"):
         profile_ops(args, torch, rs, workloads, dev)
         return None
 

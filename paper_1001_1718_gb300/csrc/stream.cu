@@ -223,7 +223,9 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
         return;
     }
 
-    // Column taps of this thread's four elements: staged position of the
+    // Column taps of this thread's four elements of the horizontal pass,
+    // qx + nq k (k = 0..3: consecutive lanes gather neighbouring staged
+    // elements, so the loads avoid bank conflicts): staged position of the
     // first tap (tap q is q * C further) and the weights, paired for FP32x2.
     int off[4];
     float2 w01[KT], w23[KT];
@@ -231,7 +233,7 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
         float wx[4][KT];
         #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int el = 4 * qx + k;
+            const int el = qx + nq * k;
             if (el < nE) {
                 const int64_t e = e0 + el;
                 const int j = (int)(e / C), c = (int)(e - (int64_t)j * C);
@@ -401,7 +403,7 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
         }
 
         // Horizontal pass over the new rows.
-        if (4 * qx < nE) {
+        if (qx < nE) {
             for (int k = ty; k < nn; k += rpp) {
                 const float* Sr = SR + k * cfg.swe_max;
                 float2 h01 = make_float2(0.0f, 0.0f), h23 = make_float2(0.0f, 0.0f);
@@ -410,8 +412,11 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
                     h01 = __ffma2_rn(w01[q], make_float2(Sr[off[0] + q * C], Sr[off[1] + q * C]), h01);
                     h23 = __ffma2_rn(w23[q], make_float2(Sr[off[2] + q * C], Sr[off[3] + q * C]), h23);
                 }
-                const int slot = (n_lo + k + kRowBias) & hmask;
-                *reinterpret_cast<float4*>(HR + slot * HRS + hpos(4 * qx)) = make_float4(h01.x, h01.y, h23.x, h23.y);
+                float* hr = HR + ((n_lo + k + kRowBias) & hmask) * HRS;
+                hr[hpos(qx)] = h01.x;
+                hr[hpos(qx + nq)] = h01.y;
+                hr[hpos(qx + 2 * nq)] = h23.x;
+                hr[hpos(qx + 3 * nq)] = h23.y;
             }
         }
         __syncthreads();
