@@ -7,8 +7,8 @@
 // the outputs whose taps land on input i form one range [jlo(i), jhi(i)];
 // border inputs also receive the clamped taps, which only widens their range.
 //
-// 1. k_adjoint_table builds, per axis, jlo(i), the range length and the
-//    summed weights w(i, j) = sum over taps q of output j with
+// 1. k_adjoint_tables builds, for both axes in one launch, jlo(i), the range
+//    length and the summed weights w(i, j) = sum over taps q of output j with
 //    clamp(first(j) + q) == i, into the caller's workspace.
 // 2. Default: two memory-bound passes per group of planes through an FP32
 //    intermediate T in the workspace: k_adj_x applies the x-axis transpose to
@@ -90,11 +90,28 @@ __device__ __forceinline__ int taps_rt(int j, int n, int m, int method, int coor
 }
 
 // One thread per input index i of an axis (n inputs, m outputs).
-__global__ void k_adjoint_table(int n, int m, int method, int coord, float a, int* lo_out, int* cnt_out,
-                                float* w_out, int K, unsigned int* fault)
+// One thread per (input index i, range slot k) of both axes in one launch:
+// entries [0, ny * yK) are the y axis, the rest the x axis. Each thread finds
+// i's output range [jlo, jhi] by binary search over the (non-decreasing)
+// first taps and writes slot k's summed weight; slot 0 also writes jlo and
+// the range length.
+struct TableAxis {
+    int n, m;          // inputs, outputs along the axis
+    int K;             // slots per input
+    int* lo;
+    int* cnt;
+    float* w;
+};
+
+__global__ void k_adjoint_tables(TableAxis ya, TableAxis xa, int method, int coord, float a, unsigned int* fault)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ny = (int64_t)ya.n * ya.K;
+    if (t >= ny + (int64_t)xa.n * xa.K) return;
+    const TableAxis& ax = t < ny ? ya : xa;
+    const int64_t u = t < ny ? t : t - ny;
+    const int i = (int)(u / ax.K), k = (int)(u - (int64_t)i * ax.K);
+    const int n = ax.n, m = ax.m;
     const int KT = method == M_NEAREST ? 1 : method == M_BILINEAR ? 2 : 4;
     // jlo = first j with first(j) >= i - KT + 1 (0 for i == 0)
     int jl = 0;
@@ -109,7 +126,7 @@ __global__ void k_adjoint_table(int n, int m, int method, int coord, float a, in
     // jhi = last j with first(j) <= i (m - 1 for i == n - 1)
     int jh = m - 1;
     if (i < n - 1) {
-        int l = 0, h = m;
+        int l = jl, h = m;
         while (l < h) {
             const int mid = (l + h) >> 1;
             if (first_tap_rt(mid, n, m, method, coord) > i) h = mid; else l = mid + 1;
@@ -117,22 +134,22 @@ __global__ void k_adjoint_table(int n, int m, int method, int coord, float a, in
         jh = l - 1;
     }
     int cnt = max(0, jh - jl + 1);
-    if (cnt > K) {
-        report_fault(fault, FAULT_BWD_TAPS);
-        cnt = K;
+    if (cnt > ax.K) {
+        if (k == 0) report_fault(fault, FAULT_BWD_TAPS);
+        cnt = ax.K;
     }
-    lo_out[i] = jl;
-    cnt_out[i] = cnt;
-    for (int k = 0; k < K; ++k) {
-        float acc = 0.0f;
-        if (k < cnt) {
-            float w[4];
-            const int f = taps_rt(jl + k, n, m, method, coord, a, w);
-            for (int q = 0; q < KT; ++q)
-                if (clampi(f + q, n) == i) acc += w[q];
-        }
-        w_out[(int64_t)i * K + k] = acc;
+    if (k == 0) {
+        ax.lo[i] = jl;
+        ax.cnt[i] = cnt;
     }
+    float acc = 0.0f;
+    if (k < cnt) {
+        float w[4];
+        const int f = taps_rt(jl + k, n, m, method, coord, a, w);
+        for (int q = 0; q < KT; ++q)
+            if (clampi(f + q, n) == i) acc += w[q];
+    }
+    ax.w[(int64_t)i * ax.K + k] = acc;
 }
 
 struct AdjTables {
@@ -504,13 +521,14 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     tb.yK = p.yK;
     tb.xK = p.xK;
     unsigned int* fw = fault_word();
-    k_adjoint_table<<<(g.H + 127) / 128, 128, 0, st>>>(g.H, g.Ho, method, g.coord, g.a, (int*)tb.ylo,
-                                                        (int*)tb.ycnt, (float*)tb.yw, tb.yK, fw);
+    {
+        const TableAxis ya{g.H, g.Ho, tb.yK, (int*)tb.ylo, (int*)tb.ycnt, (float*)tb.yw};
+        const TableAxis xa{g.W, g.Wo, tb.xK, (int*)tb.xlo, (int*)tb.xcnt, (float*)tb.xw};
+        const int64_t entries = (int64_t)g.H * tb.yK + (int64_t)g.W * tb.xK;
+        k_adjoint_tables<<<(unsigned)((entries + 127) / 128), 128, 0, st>>>(ya, xa, method, g.coord, g.a, fw);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
-    k_adjoint_table<<<(g.W + 127) / 128, 128, 0, st>>>(g.W, g.Wo, method, g.coord, g.a, (int*)tb.xlo,
-                                                        (int*)tb.xcnt, (float*)tb.xw, tb.xK, fw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     const float* dY = static_cast<const float*>(grad_out);
     float* dX = static_cast<float*>(grad_in);
     if (two_pass) {
