@@ -262,10 +262,10 @@ k_adjoint(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, co
 static constexpr int kAdjThreads = 256;
 
 // T[p][j][e] = sum_k wx[x][k] dY[p][j][(xlo(x) + k) C + c] for the dY rows
-// j of this block (e = x C + c). T has rows of W C elements. Four dY rows
-// are gathered per iteration (independent loads in flight); row offsets
-// within a plane are 32-bit (the host bounds Ho x pitch below 2^31).
-template <int KXM>
+// j of this block (e = x C + c). T has rows of W C elements. RU dY rows are
+// gathered per iteration (independent loads in flight); row offsets within
+// a plane are 32-bit (the host bounds Ho x pitch below 2^31).
+template <int KXM, int RU>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adj_x(const Geom g, const float* __restrict__ dY, float* __restrict__ T, const AdjTables tb, int plane0,
         int rows_per_thread)
@@ -285,20 +285,22 @@ k_adj_x(const Geom g, const float* __restrict__ dY, float* __restrict__ T, const
     const int pitch = (int)g.dst_pitch;
     const int j0 = blockIdx.y * rows_per_thread, j1 = min(g.Ho, j0 + rows_per_thread);
     int j = j0;
-    for (; j + 4 <= j1; j += 4) {
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (; j + RU <= j1; j += RU) {
+        float acc[RU];
+        #pragma unroll
+        for (int r = 0; r < RU; ++r) acc[r] = 0.0f;
         #pragma unroll
         for (int k = 0; k < KXM; ++k) {
             if (k < cnt) {
-                float v[4];
+                float v[RU];
                 #pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = __ldg(src + (j + r) * pitch + k * g.C);
+                for (int r = 0; r < RU; ++r) v[r] = __ldg(src + (j + r) * pitch + k * g.C);
                 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] = fmaf(w[k], v[r], acc[r]);
+                for (int r = 0; r < RU; ++r) acc[r] = fmaf(w[k], v[r], acc[r]);
             }
         }
         #pragma unroll
-        for (int r = 0; r < 4; ++r) dst[(j + r) * WC] = acc[r];
+        for (int r = 0; r < RU; ++r) dst[(j + r) * WC] = acc[r];
     }
     for (; j < j1; ++j) {
         const float* row = src + j * pitch;
@@ -533,7 +535,10 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     float* dX = static_cast<float*>(grad_in);
     if (two_pass) {
         float* T = reinterpret_cast<float*>(ws + p.off_t);
+        // rows per thread: x pass 8 (4 per iteration) for up to 4 taps, 16 (8
+        // per iteration) beyond; y pass 8
         const int rpt = 8;
+        const int rpx = KX <= 4 ? 8 : 16;
         const int WC = g.W * g.C;
         const unsigned gx = (unsigned)((WC + kAdjThreads - 1) / kAdjThreads);
         // 16-byte y-pass rows: whole float4s in every T and dX row.
@@ -543,11 +548,11 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
         const unsigned gy = (unsigned)((WC / V + kAdjThreads - 1) / kAdjThreads);
         for (int p0 = 0; p0 < g.planes; p0 += p.group_planes) {
             const int np = std::min(p.group_planes, g.planes - p0);
-            dim3 gxg(gx, (unsigned)((g.Ho + rpt - 1) / rpt), (unsigned)np);
-            if (KX <= 4) k_adj_x<4><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
-            else if (KX <= 8) k_adj_x<8><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
-            else if (KX <= 16) k_adj_x<16><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
-            else k_adj_x<32><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpt);
+            dim3 gxg(gx, (unsigned)((g.Ho + rpx - 1) / rpx), (unsigned)np);
+            if (KX <= 4) k_adj_x<4, 4><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpx);
+            else if (KX <= 8) k_adj_x<8, 8><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpx);
+            else if (KX <= 16) k_adj_x<16, 8><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpx);
+            else k_adj_x<32, 8><<<gxg, kAdjThreads, 0, st>>>(g, dY, T, tb, p0, rpx);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
             dim3 gyg(gy, (unsigned)((g.H + rpt - 1) / rpt), (unsigned)np);
             const int KY = p.yK;
