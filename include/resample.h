@@ -166,7 +166,7 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
  * grad_in is OVERWRITTEN. `workspace` is a device buffer of at least the
  * size rs_resize_backward_workspace() reports: the per-axis transposed weight
  * tables and an FP32 intermediate (the x-transposed rows of a group of
- * planes, at most ~64 MB); it is written by the call and may be reused after
+ * planes, at most ~256 MB); it is written by the call and may be reused after
  * the call's work on `stream` has finished. opt->impl = RS_IMPL_TILED selects
  * the single-pass tiled kernel instead (tables only are used).
  */

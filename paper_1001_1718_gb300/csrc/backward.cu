@@ -367,7 +367,7 @@ struct BwdPlan {
     int group_planes;
 };
 
-static constexpr size_t kAdjTBudget = (size_t)64 << 20;   // bytes of T per plane group
+static constexpr size_t kAdjTBudget = (size_t)256 << 20;  // bytes of T per plane group
 
 static BwdPlan plan_tables(const Geom& g, int method)
 {

@@ -138,13 +138,16 @@ def test_workspace_errors(rs):
 def test_plane_groups_and_large_upscale(rs, oracle):
     """More planes than one intermediate group holds, and a x6 upscale
     (wide transposed rows)."""
-    g = torch.randn(40, 3, 600, 700, device="cuda")      # 120 planes of 600x700 -> groups
-    gi = rs.resize_backward(g, (300, 350), "bicubic")
+    # 48 planes whose x-adjoint intermediates (2048 x 768 FP32, 6.3 MB each)
+    # exceed one 256 MB group
+    g = torch.randn(16, 3, 2048, 1536, device="cuda")
+    gi = rs.resize_backward(g, (1024, 768), "bicubic")
     torch.cuda.synchronize()
-    for (n, c) in ((0, 0), (39, 2), (17, 1)):
-        ref = oracle.adjoint(g[n, c].cpu().numpy().astype(np.float64), 300, 350, 2)[:, :, 0]
-        tol = _tol(oracle, 300, 350, 600, 700, 2, 0, float(g[n, c].abs().max()))
+    for (n, c) in ((0, 0), (15, 2), (13, 1)):
+        ref = oracle.adjoint(g[n, c].cpu().numpy().astype(np.float64), 1024, 768, 2)[:, :, 0]
+        tol = _tol(oracle, 1024, 768, 2048, 1536, 2, 0, float(g[n, c].abs().max()))
         assert np.abs(gi[n, c].cpu().numpy() - ref).max() <= tol
+    del g, gi
     g6 = torch.randn(1, 1, 120, 180, device="cuda")
     gi6 = rs.resize_backward(g6, (20, 30), "bicubic", coord="half_pixel")
     ref = oracle.adjoint(g6[0, 0].cpu().numpy().astype(np.float64), 20, 30, 2, 1)[:, :, 0]
