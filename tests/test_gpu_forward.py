@@ -275,3 +275,32 @@ def test_gather_staged_rows(rs, oracle, dtype, band):
         check(y, oracle.resize(x64, Ho, Wo, NN, coord), dtype, NN, 1.0, f"staged {dtype} {band} {H}x{W}x{C}->{Ho}x{Wo}")
         assert torch.equal(y, rs.resize(t.cuda(), (Ho, Wo), "nearest", coord=CNAME[coord], impl="tiled"))
     assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
+def test_window_shifted_staging(rs, oracle, dtype):
+    """The register-window kernel on source rows that are not whole 16-byte
+    units (odd widths, NCHW planes starting mid-unit, a pitched view whose
+    first row starts mid-unit): the shifted copies and their element-wise
+    fill at the plane's first and last rows, against the oracle and the
+    tiled kernel, bit for bit."""
+    for k, (N, C, H, W, Ho, Wo, method, coord) in enumerate([(2, 3, 75, 131, 150, 262, BC, 0),
+                                                              (1, 2, 41, 67, 123, 201, BL, 1),
+                                                              (3, 1, 33, 19, 70, 45, BC, 1)]):
+        t, x64 = _src(1200 + k, (N, C, H, W), dtype)
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="window",
+                      tile=(1024, 4))
+        torch.cuda.synchronize()
+        check(y, oracle.resize_nchw(x64, Ho, Wo, method, coord), dtype, method, np.abs(x64).max(),
+              f"shifted nchw {dtype} {(N, C, H, W)}->{Ho}x{Wo}")
+        ref = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="tiled")
+        assert torch.equal(y, ref)
+    # an interleaved view whose rows start one element into a wider buffer
+    t, x64 = _src(1300, (97, 211, 3), dtype)
+    big = torch.zeros((97, 215, 3), dtype=t.dtype)
+    big[:, 1:212] = t
+    view = big.cuda()[:, 1:212]
+    y = rs.resize(view, (190, 400), "bicubic", impl="window", tile=(1024, 8))
+    torch.cuda.synchronize()
+    check(y, oracle.resize(x64, 190, 400, BC, 0), dtype, BC, np.abs(x64).max(), f"shifted view {dtype}")
+    assert rs.debug_fault() == 0
