@@ -68,9 +68,10 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
  *          by 256) of a 1024-element strip for a whole band of rows and keeps the
  *          horizontally interpolated source rows its taps need in registers,
  *          so each output row is blended without touching shared memory;
- *          source rows are staged in chunks of tile_h rows (double
- *          buffered, next chunk's loads in flight); waves = blocks per
- *          resident block slot (sets the band height).
+ *          source rows are staged in chunks of tile_h rows (a multiple of
+ *          the taps: 2 bilinear, 4 bicubic; double buffered, the next two
+ *          chunks' copies in flight); waves = blocks per resident block slot
+ *          (sets the band height).
  * STREAM = one block per (column strip, band of rows), walking down the band
  *          in chunks; every source row is staged and horizontally
  *          interpolated once per strip; loads of the next chunk are issued
@@ -201,7 +202,8 @@ typedef struct {
  *   dtype, count and coord) its shape is used instead. An explicit tile_w /
  *   tile_h / threads tiles every image.
  * impl = RS_IMPL_WINDOW: window items with band = tile_w output rows
- *   (1..256, 0 = 256) and chunk = tile_h staged rows (4..32, 0 = 8 else 4);
+ *   (1..256, 0 = 256) and chunk = tile_h staged rows (4..32, a multiple of
+ *   the taps, 0 = 8 else 4);
  *   images that do not fit are tiled.
  * impl = RS_IMPL_TILED: every image as tiles of tile_w elements (0 = 512)
  *   x at most tile_h rows (0 = 32) with `threads` threads (0 = 256).

@@ -42,7 +42,7 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
     if (method != M_BILINEAR && method != M_BICUBIC) return false;
     const int KT = method_taps(method);
     const int es = (int)dtype_size(dtype);
-    if (c.chunk < KT) return false;
+    if (c.chunk < KT || c.chunk % KT) return false;   // chunks hold whole groups of KT positions
     const uintptr_t basep = reinterpret_cast<uintptr_t>(src);
     const bool planar = g.sp.cp > 1 || g.planes > 1;
     // 16-byte-aligned rows of whole units (1), else the shifted copies (2).

@@ -419,7 +419,11 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
         for (int u = 0; u < KT; ++u) {
             if (b <= b_last) {
                 // Make source row r = b + KT - 1 available in the staged chunk.
-                if (r >= chunk_lo + nn) {
+                // Chunk c starts at row r_first + c R and r = b + KT - 1 starts
+                // at r_first + KT - 1, so with R a multiple of KT (the host's
+                // rule) a chunk is entered only at u == 1: one copy of the
+                // switch code per unrolled group.
+                if (u == 1 && r >= chunk_lo + nn) {
                     // Move to chunk c = cidx + 1. Its FP32 half held chunk c-2,
                     // whose reads all precede the barrier of the previous
                     // switch; its raw slot was filled two switches ago (wait
