@@ -168,8 +168,17 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
  * size rs_resize_backward_workspace() reports: the per-axis transposed weight
  * tables and an FP32 intermediate (the x-transposed rows of a group of
  * planes, at most ~256 MB); it is written by the call and may be reused after
- * the call's work on `stream` has finished. opt->impl = RS_IMPL_TILED selects
- * the single-pass tiled kernel instead (tables only are used).
+ * the call's work on `stream` has finished. Kernels (opt->impl):
+ *   RS_IMPL_AUTO   - WINDOW where it applies, else STREAM, else TILED;
+ *   RS_IMPL_WINDOW - one fused pass: each thread keeps the x-transposed
+ *                    dY rows its y taps need in registers (at most 8
+ *                    transposed taps per axis, dY rows of whole aligned
+ *                    16-byte units; RS_ERR_INVALID_ARG otherwise); same
+ *                    results as STREAM;
+ *   RS_IMPL_STREAM - two passes through the intermediate (x, then y);
+ *   RS_IMPL_TILED  - one tiled pass through shared memory.
+ * Only the tables (and, for STREAM, the intermediate) of the workspace are
+ * used.
  */
 rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in,
                                        rs_method method, const rs_options* opt,

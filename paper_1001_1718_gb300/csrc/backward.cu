@@ -355,6 +355,186 @@ k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const
 }
 
 // ---------------------------------------------------------------------------
+// Fused register-window adjoint (FP32, dY rows of whole 16-byte units).
+//
+// The transpose of the forward's register window. A block owns a strip of
+// 2 x 256 dX elements and a band of dX rows; thread t owns elements t and
+// t + 256. It walks the rows of T = dY Ax that the band's y taps reach
+// ("positions"): each dY row, staged in shared memory, is x-adjointed at
+// the thread's two columns into a register window of the last KY such
+// rows, and every dX row whose first y tap is the window's first row is
+// blended from registers and stored. dY rows are copied with 16-byte
+// cp.async in chunks of R rows into a three-slot ring two chunks ahead and
+// read in place. The sums run in the two-pass order (x taps, then y taps,
+// each ascending), so the results equal the two-pass kernels'.
+struct AdjWinCfg {
+    int band_h, band_cap, pos_cap, chunk, swe_max;
+    size_t smem;
+};
+static constexpr int kAwThreads = 256;
+static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
+
+template <int C, int KX, int KY>
+__global__ void __launch_bounds__(kAwThreads, 2)
+k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, const AdjTables tb,
+             const AdjWinCfg cfg, unsigned int* fault)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int tid = threadIdx.x;
+    const int plane = blockIdx.z;
+    const float* s = dY + g.dp.offset(plane);   // Ho rows of Wo C, pitch dst_pitch
+    float* d = dX + g.sp.offset(plane);         // H rows of W C, pitch src_pitch
+    const int WC = g.W * C, WoC = g.Wo * C;
+    const int e0 = blockIdx.x * kAwElems;
+    const int nE = min(kAwElems, WC - e0);
+    const int yb = blockIdx.y * cfg.band_h;
+    const int nrows = min(cfg.band_h, g.H - yb);
+
+    // dY columns under the strip: [a0, c_hi), a0 on a 16-byte boundary; the
+    // columns past the row (x taps beyond a range, zero weights) read zeros.
+    const int x_first = e0 / C, x_last = (e0 + nE - 1) / C;
+    const int a0 = (__ldg(tb.xlo + x_first) * C) & ~3;
+    const int c_hi = (__ldg(tb.xlo + x_last) + KX) * C;
+    const int in_hi = min(c_hi, WoC);
+    const int units = (in_hi - a0 + 3) / 4;
+    const int R = cfg.chunk;
+    if (c_hi - a0 > cfg.swe_max || nrows > cfg.band_cap || R < KY || R % KY) {   // uniform
+        if (tid == 0) report_fault(fault, FAULT_BWD_SPAN);
+        return;
+    }
+    float* RING = sm;                                            // [3][R][swe_max]
+    float* RW = RING + 3 * R * cfg.swe_max;                      // [band_cap][KY]
+    int* RF = reinterpret_cast<int*>(RW + cfg.band_cap * KY);    // [band_cap] first y taps
+    int* NC = RF + cfg.band_cap;                                 // [pos_cap] rows per position
+    if (c_hi > WoC) {
+        const int z0 = WoC - a0, zn = c_hi - WoC;
+        for (int u = tid; u < 3 * R * zn; u += kAwThreads) {
+            const int row = u / zn;
+            RING[row * cfg.swe_max + z0 + (u - row * zn)] = 0.0f;
+        }
+    }
+    for (int i = tid; i < nrows; i += kAwThreads) {
+        const int r = yb + i;
+        RF[i] = __ldg(tb.ylo + r);
+        const int cnt = __ldg(tb.ycnt + r);
+        #pragma unroll
+        for (int p = 0; p < KY; ++p) RW[i * KY + p] = p < cnt ? __ldg(tb.yw + (int64_t)r * tb.yK + p) : 0.0f;
+    }
+    // x taps of this thread's two elements, paired for FP32x2
+    int off[2];
+    float2 wxp[KX];
+    {
+        float wx[2][KX];
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int el = tid + kAwThreads * k;
+            if (el < nE) {
+                const int e = e0 + el, x = e / C, c = e - x * C;
+                const int lo = __ldg(tb.xlo + x), cnt = __ldg(tb.xcnt + x);
+                off[k] = lo * C + c - a0;
+                #pragma unroll
+                for (int q = 0; q < KX; ++q) wx[k][q] = q < cnt ? __ldg(tb.xw + (int64_t)x * tb.xK + q) : 0.0f;
+            } else {
+                off[k] = 0;
+                #pragma unroll
+                for (int q = 0; q < KX; ++q) wx[k][q] = 0.0f;
+            }
+        }
+        #pragma unroll
+        for (int q = 0; q < KX; ++q) wxp[q] = make_float2(wx[0][q], wx[1][q]);
+    }
+    for (int p = tid; p < cfg.pos_cap; p += kAwThreads) NC[p] = 0;
+    __syncthreads();
+    const int b_first = RF[0], b_last = RF[nrows - 1];
+    if (b_last - b_first + 1 > cfg.pos_cap) {   // uniform; the host bounds the positions
+        if (tid == 0) report_fault(fault, FAULT_BWD_SPAN);
+        return;
+    }
+    for (int i0 = tid; i0 < nrows; i0 += kAwThreads) {
+        if (i0 == 0 || RF[i0] != RF[i0 - 1]) {
+            int len = 1;
+            while (i0 + len < nrows && RF[i0 + len] == RF[i0]) ++len;
+            NC[RF[i0] - b_first] = len;
+        }
+    }
+    // dY rows b_first .. b_last + KY - 1 (past the last row: the last row,
+    // under zero weights), in chunks of R.
+    const int r_first = b_first, r_end = b_last + KY;
+    auto chunk_rows = [&](int c) { return max(0, min(R, r_end - (r_first + c * R))); };
+    const uint32_t umul = units > 1 ? 0xFFFFFFFFu / (uint32_t)units + 1u : 0u;
+    auto issue = [&](int c) {
+        const int r0 = r_first + c * R, nn = chunk_rows(c);
+        float* slot = RING + (c % 3) * R * cfg.swe_max;
+        for (int u = tid; u < nn * units; u += kAwThreads) {
+            const int k = units > 1 ? (int)__umulhi((uint32_t)u, umul) : u;
+            const int w = u - k * units;
+            const float* src = s + (int64_t)clampi(r0 + k, g.Ho) * g.dst_pitch + a0 + 4 * w;
+            const unsigned sdst = (unsigned)__cvta_generic_to_shared(slot + k * cfg.swe_max + 4 * w);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    issue(1);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();   // chunk 0 and the position table visible
+    issue(2);
+
+    auto hrow = [&](const float* Sr, float2& h) {
+        h = make_float2(0.0f, 0.0f);
+        #pragma unroll
+        for (int q = 0; q < KX; ++q) h = __ffma2_rn(wxp[q], make_float2(Sr[off[0] + q * C], Sr[off[1] + q * C]), h);
+    };
+    float2 h[KY];
+    #pragma unroll
+    for (int p = 0; p < KY - 1; ++p) hrow(RING + p * cfg.swe_max, h[p]);
+    int r = b_first + KY - 1, cidx = 0, chunk_lo = r_first;
+    int nn = chunk_rows(0);
+    int i = 0, b = b_first;
+    const int nact = (tid < nE) + (tid + kAwThreads < nE);
+    float* const dband = d + (int64_t)yb * g.src_pitch + e0 + tid;
+    const int pitch32 = (int)g.src_pitch;
+    auto blend_put = [&](int row, const int* slot) {
+        float2 v = make_float2(0.0f, 0.0f);
+        #pragma unroll
+        for (int p = 0; p < KY; ++p) {
+            const float w = RW[row * KY + p];
+            v = __ffma2_rn(make_float2(w, w), h[slot[p]], v);
+        }
+        float* q = dband + row * pitch32;
+        if (nact > 0) q[0] = v.x;
+        if (nact > 1) q[kAwThreads] = v.y;
+    };
+    while (b <= b_last) {
+        #pragma unroll
+        for (int u = 0; u < KY; ++u) {
+            if (b <= b_last) {
+                // with R a multiple of KY a chunk is entered only at u == 1
+                if (u == 1 % KY && r >= chunk_lo + nn) {
+                    ++cidx;
+                    chunk_lo = r_first + cidx * R;
+                    nn = chunk_rows(cidx);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                    __syncthreads();   // chunk cidx visible; chunk cidx - 1 no longer read
+                    issue(cidx + 2);
+                }
+                const int ns = (u + KY - 1) % KY;
+                hrow(RING + ((cidx % 3) * R + (r - chunk_lo)) * cfg.swe_max, h[ns]);
+                ++r;
+                int slot[KY];
+                #pragma unroll
+                for (int p = 0; p < KY; ++p) slot[p] = (u + p) % KY;
+                const int nb = NC[b - b_first];
+                for (int k = 0; k < nb; ++k) blend_put(i + k, slot);
+                i += nb;
+                ++b;
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -418,6 +598,77 @@ static bool adj_config(const Geom& g, const BwdPlan& p, int TH, AdjCfg& cfg)
     cfg.smem = sizeof(float) * ((size_t)cfg.fh_max * cfg.fwe_max + (size_t)cfg.fh_max * cfg.tile_w +
                                 (size_t)TH * p.yK) + sizeof(int) * 2 * (size_t)TH;
     return cfg.smem <= max_smem_per_block();
+}
+
+static int adj_taps_class(int k) { return k <= 2 ? 2 : k <= 4 ? 4 : 8; }
+
+// The fused window adjoint applies with at most 8 transposed taps per axis,
+// dY rows of whole 16-byte units and a footprint that fits shared memory.
+static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, AdjWinCfg& c)
+{
+    if (p.xK > 8 || p.yK > 8) return false;
+    const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
+    if (reinterpret_cast<uintptr_t>(dY) % 16 || g.dst_pitch % 4 || ((int64_t)g.Wo * g.C) % 4) return false;
+    if (g.planes > 1 && (g.dp.n_stride % 4 || g.dp.c_stride % 4)) return false;
+    c.chunk = std::max(4, KY);
+    const int WC = g.W * g.C;
+    int swe = 4;
+    for (int e0 = 0; e0 < WC; e0 += kAwElems) {
+        const int nE = std::min(kAwElems, WC - e0);
+        const int xf = e0 / g.C, xl = (e0 + nE - 1) / g.C;
+        const int a0 = (p.rx.lo[xf] * g.C) & ~3;
+        swe = std::max(swe, (p.rx.lo[xl] + KX) * g.C - a0);
+    }
+    c.swe_max = (swe + 3) & ~3;
+    c.band_cap = std::min(256, g.H);
+    int pos = 1;
+    for (int i = 0; i < g.H; ++i) {
+        const int last = std::min(g.H - 1, i + c.band_cap - 1);
+        pos = std::max(pos, p.ry.lo[last] - p.ry.lo[i] + 1);
+    }
+    c.pos_cap = pos;
+    if ((int64_t)c.band_cap * g.src_pitch >= (int64_t)INT32_MAX) return false;   // 32-bit row offsets
+    c.smem = sizeof(float) * (3 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KY) +
+             sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);
+    c.band_h = 0;
+    return c.smem <= max_smem_per_block();
+}
+
+template <int C, int KX, int KY>
+static void* adj_window_func() { return reinterpret_cast<void*>(&k_adj_window<C, KX, KY>); }
+
+template <int C, int KX>
+static void* adj_window_fy(int KY)
+{
+    return KY == 2 ? adj_window_func<C, KX, 2>() : KY == 4 ? adj_window_func<C, KX, 4>() : adj_window_func<C, KX, 8>();
+}
+
+template <int C>
+static void* adj_window_fx(int KX, int KY)
+{
+    return KX == 2 ? adj_window_fy<C, 2>(KY) : KX == 4 ? adj_window_fy<C, 4>(KY) : adj_window_fy<C, 8>(KY);
+}
+
+static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const float* dY, float* dX, const AdjTables& tb,
+                                     AdjWinCfg c, cudaStream_t st)
+{
+    const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
+    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY) : g.C == 2 ? adj_window_fx<2>(KX, KY)
+               : g.C == 3 ? adj_window_fx<3>(KX, KY) : adj_window_fx<4>(KX, KY);
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kAwThreads, c.smem);
+    if (e != cudaSuccess) return e;
+    const int64_t strips = ((int64_t)g.W * g.C + kAwElems - 1) / kAwElems;
+    const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
+    const int64_t bands = std::max<int64_t>(1, (2 * resident + strips * g.planes - 1) / (strips * g.planes));
+    c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.H + bands - 1) / bands));
+    dim3 grid((unsigned)strips, (unsigned)((g.H + c.band_h - 1) / c.band_h), (unsigned)g.planes);
+    unsigned int* fw = fault_word();
+    void* args[] = {const_cast<Geom*>(&g), const_cast<float**>(&dY), &dX, const_cast<AdjTables*>(&tb), &c, &fw};
+    e = cudaLaunchKernel(func, grid, dim3(kAwThreads), args, c.smem, st);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int KX, int C>
@@ -497,15 +748,23 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     }
     const int KX = p.xK;
     if (KX > 64) return RS_ERR_UNSUPPORTED;   // > 16x upscale along x
-    // Two passes by default (they measure faster than the tiled kernel at
-    // both x2 and x0.5); they use 32-bit offsets within a plane and index
-    // the y taps with at most 32 entries.
-    const bool two_pass = o.impl != RS_IMPL_TILED && KX <= 32 && p.yK <= 32 &&
+    // AUTO: the fused window adjoint where it applies, else the two passes
+    // (faster than the tiled kernel at both x2 and x0.5), else the tiled
+    // kernel. RS_IMPL_WINDOW / RS_IMPL_STREAM / RS_IMPL_TILED select one
+    // (the window adjoint is refused where it does not apply). The two
+    // passes use 32-bit offsets within a plane and index the y taps with
+    // at most 32 entries.
+    AdjWinCfg wcfg;
+    const bool window_ok = (o.impl == RS_IMPL_AUTO || o.impl == RS_IMPL_WINDOW) &&
+                           adj_window_config(g, p, grad_out, wcfg);
+    if (o.impl == RS_IMPL_WINDOW && !window_ok) return RS_ERR_INVALID_ARG;
+    if (o.impl == RS_IMPL_PLAIN || o.impl == RS_IMPL_GATHER) return RS_ERR_INVALID_ARG;
+    const bool two_pass = !window_ok && o.impl != RS_IMPL_TILED && KX <= 32 && p.yK <= 32 &&
                           (int64_t)g.Ho * g.dst_pitch < (int64_t)INT32_MAX &&
                           (int64_t)g.H * g.src_pitch < (int64_t)INT32_MAX &&
                           (int64_t)g.Ho * g.W * g.C < (int64_t)INT32_MAX;
     AdjCfg cfg;
-    if (!two_pass) {
+    if (!window_ok && !two_pass) {
         bool ok = false;
         for (int TH = 32; TH >= 1 && !ok; TH >>= 1) ok = adj_config(g, p, TH, cfg);
         if (!ok) return RS_ERR_UNSUPPORTED;
@@ -533,6 +792,7 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
     if (e != cudaSuccess) return cuda_status(e);
     const float* dY = static_cast<const float*>(grad_out);
     float* dX = static_cast<float*>(grad_in);
+    if (window_ok) return cuda_status(launch_adj_window(g, p, dY, dX, tb, wcfg, st));
     if (two_pass) {
         float* T = reinterpret_cast<float*>(ws + p.off_t);
         // rows per thread: x pass 8 (4 per iteration) for up to 4 taps, 16 (8

@@ -152,3 +152,44 @@ def test_plane_groups_and_large_upscale(rs, oracle):
     gi6 = rs.resize_backward(g6, (20, 30), "bicubic", coord="half_pixel")
     ref = oracle.adjoint(g6[0, 0].cpu().numpy().astype(np.float64), 20, 30, 2, 1)[:, :, 0]
     assert np.abs(gi6[0, 0].cpu().numpy() - ref).max() <= _tol(oracle, 20, 30, 120, 180, 2, 1, float(g6.abs().max()))
+
+
+# scales up to 2 (at most 8 transposed bicubic taps per axis), dY rows of
+# whole 16-byte units
+WIN_SHAPES = [(37, 54, 74, 108), (64, 48, 32, 24), (31, 29, 52, 56), (40, 40, 40, 40), (300, 258, 600, 516),
+              (120, 90, 20, 12), (1, 17, 3, 32), (200, 150, 400, 300)]
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("coord", [0, 1])
+def test_window_adjoint(rs, oracle, method, coord):
+    """The fused register-window adjoint (dY rows of whole 16-byte units, at
+    most 8 transposed taps per axis) against the oracle's adjoint, and equal
+    to the two-pass kernels, whose sums it runs in the same order."""
+    for k, (H, W, Ho, Wo) in enumerate(WIN_SHAPES):
+        g = np.random.default_rng(300 + k).standard_normal((2, 3, Ho, Wo)).astype(np.float32)
+        gt = torch.from_numpy(g).cuda()
+        gi = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord], impl="window")
+        two = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord], impl="stream")
+        torch.cuda.synchronize()
+        ref = oracle.adjoint_nchw(g.astype(np.float64), H, W, method, coord)
+        err = np.abs(gi.cpu().numpy().astype(np.float64) - ref).max()
+        tol = _tol(oracle, H, W, Ho, Wo, method, coord, np.abs(g).max())
+        assert err <= tol, f"{MN[method]} {CN[coord]} {H}x{W}<-{Ho}x{Wo}: {err} > {tol}"
+        assert torch.equal(gi, two), f"window vs two-pass {MN[method]} {CN[coord]} {H}x{W}<-{Ho}x{Wo}"
+    # interleaved channels
+    for C in (1, 3, 4):
+        g = np.random.default_rng(9).standard_normal((90, 132, C)).astype(np.float32)
+        gt = torch.from_numpy(g).cuda()
+        gi = rs.resize_backward(gt, (45, 66), MN[method], layout="hwc", coord=CN[coord], impl="window")
+        two = rs.resize_backward(gt, (45, 66), MN[method], layout="hwc", coord=CN[coord], impl="stream")
+        torch.cuda.synchronize()
+        assert torch.equal(gi, two)
+        ref = oracle.adjoint(g.astype(np.float64), 45, 66, method, coord)
+        assert np.abs(gi.cpu().numpy() - ref).max() <= _tol(oracle, 45, 66, 90, 132, method, coord, np.abs(g).max())
+    # not applicable: more than 8 transposed taps along x (bicubic x3), odd dY rows
+    with pytest.raises(rs.ResampleError):
+        rs.resize_backward(torch.randn(1, 1, 60, 60, device="cuda"), (20, 20), "bicubic", impl="window")
+    with pytest.raises(rs.ResampleError):
+        rs.resize_backward(torch.randn(1, 1, 40, 41, device="cuda"), (20, 20), "bilinear", impl="window")
+    assert rs.debug_fault() == 0
