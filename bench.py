@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="tune tile shapes before timing")
+    ap.add_argument("--tile-sweep", action="store_true",
+                    help="the paper's tiling experiment on this GPU: an 800x800 uint8 image, bilinear at scales "
+                         "2..10, the paper's kernel (one thread per output pixel) over block shapes, against "
+                         "AUTO; prints a markdown table and exits")
     ap.add_argument("--ops-only", nargs="?", const="headline", default=None,
                     choices=["headline", "nchw", "backward", "batch"],
                     help="profiling driver: run warmup + steps of the three headline resizes (headline), "
@@ -624,8 +628,52 @@ def run_reference(args, rank, world):
             "gpu_launches": 0}
 
 
+def tile_sweep():
+    """The tiling study of the paper (Sec. IV-V: one thread per output pixel,
+    the block shape decides the time) replayed on this GPU: 800x800 uint8
+    single-channel source from the uniform generator, bilinear x2..x10 with
+    the plain kernel over block shapes, and the AUTO kernel beside it.
+    Median of 20 CUDA-event timed launches, L2 flushed before each."""
+    import torch
+    import paper_1001_1718_gb300 as rs
+    from paper_1001_1718_gb300 import workloads
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = Flusher(torch, dev)
+    img = workloads.uniform_u8(6, 800, 800, 1)
+    x = torch.from_numpy(img).to(dev)
+    shapes = [(32, 4), (4, 32), (16, 8), (8, 16), (8, 8), (16, 16), (32, 8), (64, 4), (128, 1), (32, 32)]
+    scales = (2, 4, 6, 8, 10)
+    rows = {}
+    for sc in scales:
+        n = 800 * sc
+        y = torch.empty((n, n, 1), dtype=torch.uint8, device=dev)
+        for (bw, bh) in shapes + [(0, 0)]:   # (0, 0): AUTO
+            impl = "plain" if bw else "auto"
+            fn = (lambda: rs.resize(x, (n, n), "bilinear", out=y, impl="plain", tile=(bw, bh))) if bw else \
+                 (lambda: rs.resize(x, (n, n), "bilinear", out=y))
+            t = time_ops(torch, stream, [("op", fn)], 20, 3, flush)["op"]
+            rows.setdefault((bw, bh) if bw else "auto", {})[sc] = statistics.median(t)
+    out = ["| kernel / block (w x h) | " + " | ".join(f"x{sc} ({800 * sc}^2) us" for sc in scales) + " |",
+           "|---|" + "---|" * len(scales)]
+    for key, d in rows.items():
+        name = "AUTO (" + rs.tile_config(x, (1600, 1600), "bilinear")["impl"] + " at x2)" if key == "auto" \
+            else f"plain {key[0]}x{key[1]}"
+        best = {sc: min(rows[k][sc] for k in rows if k != "auto") for sc in scales}
+        cells = []
+        for sc in scales:
+            v = d[sc] * 1e3
+            mark = " **best plain**" if key != "auto" and d[sc] == best[sc] else ""
+            cells.append(f"{v:.1f}{mark}")
+        out.append(f"| {name} | " + " | ".join(cells) + " |")
+    print("\n".join(out))
+
+
 def main():
     args = parse()
+    if args.tile_sweep:
+        tile_sweep()
+        return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", 0))
         world = int(os.environ.get("WORLD_SIZE", args.gpus))
