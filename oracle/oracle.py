@@ -164,6 +164,72 @@ def axis_taps(n: int, m: int, method: int, coord: int = ASYMMETRIC, a: float = -
     return idx, w
 
 
+# ---------------------------------------------------------------------------
+# Antialiased resampling (an extension: the paper samples point-wise, Eqs.
+# 1-5, and says nothing about filtering before a downscale). Reading used:
+# the interpolation kernel is stretched by the downscale factor, so every
+# output averages the source footprint it covers, and taps that fall outside
+# the image are dropped and the rest renormalised.
+#   f = max(n / m, 1) (stretch; 1 when upsampling), R = 1 (triangle, the
+#   bilinear kernel) or 2 (Keys' cubic with parameter a);
+#   centre of output j in source pixel units: c = (j + 1/2) n / m;
+#   taps i = floor(c - R f + 1/2) .. floor(c + R f + 1/2) - 1, cut to [0, n);
+#   weight of tap i: K((i + 1/2 - c) / f), divided by the sum over the taps.
+# Written out in FP64 as dense per-axis matrices; the image is
+# Ay X Ax^T per channel (a matrix product).
+# ---------------------------------------------------------------------------
+
+def _keys(u: np.ndarray, a: float) -> np.ndarray:
+    u = np.abs(u)
+    out = np.zeros_like(u)
+    m1 = u <= 1
+    m2 = (u > 1) & (u < 2)
+    out[m1] = ((a + 2) * u[m1] - (a + 3)) * u[m1] ** 2 + 1
+    out[m2] = ((a * u[m2] - 5 * a) * u[m2] + 8 * a) * u[m2] - 4 * a
+    return out
+
+
+def aa_axis_matrix(n: int, m: int, method: int, a: float = -0.5) -> np.ndarray:
+    """(m, n) FP64 antialias weights of one axis (method BILINEAR or BICUBIC)."""
+    if method not in (BILINEAR, BICUBIC):
+        raise ValueError("antialias is defined for bilinear and bicubic")
+    R = 1.0 if method == BILINEAR else 2.0
+    f = max(n / m, 1.0)
+    A = np.zeros((m, n), np.float64)
+    for j in range(m):
+        c = (j + 0.5) * n / m
+        lo = max(int(np.floor(c - R * f + 0.5)), 0)
+        hi = min(int(np.floor(c + R * f + 0.5)), n)
+        i = np.arange(lo, hi, dtype=np.float64)
+        u = (i + 0.5 - c) / f
+        w = np.maximum(0.0, 1.0 - np.abs(u)) if method == BILINEAR else _keys(u, a)
+        tot = w.sum()
+        if tot != 0.0:
+            w = w / tot
+        A[j, lo:hi] = w
+    return A
+
+
+def resize_aa(src, Ho: int, Wo: int, method: int, a: float = -0.5) -> np.ndarray:
+    """FP64 antialiased resampling of an (H, W) or (H, W, C) image; (Ho, Wo, C)."""
+    x = _hwc(src)
+    H, W, C = x.shape
+    Ay = aa_axis_matrix(H, Ho, method, a)
+    Ax = aa_axis_matrix(W, Wo, method, a)
+    out = np.empty((Ho, Wo, C), np.float64)
+    for c in range(C):
+        out[:, :, c] = Ay @ x[:, :, c] @ Ax.T
+    return out
+
+
+def resize_aa_nchw(x, Ho: int, Wo: int, method: int, a: float = -0.5) -> np.ndarray:
+    N, C, H, W = x.shape
+    Ay = aa_axis_matrix(H, Ho, method, a)
+    Ax = aa_axis_matrix(W, Wo, method, a)
+    x = np.asarray(x, np.float64)
+    return np.einsum("ih,nchw,jw->ncij", Ay, x, Ax, optimize=True)
+
+
 def quantize_u8(v) -> np.ndarray:
     x = np.ascontiguousarray(v, np.float64)
     out = np.empty(x.shape, np.uint8)

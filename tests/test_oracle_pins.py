@@ -366,3 +366,44 @@ def test_bf16_rounding_is_nearest_even(oracle):
         for nb in (int(bits) - 1, int(bits) + 1):       # neighbouring bf16 codes
             e2 = abs(fv - Fraction(_bf16_value(nb & 0xFFFF)))
             assert err < e2 or (err == e2 and (int(bits) & 1) == 0)
+
+
+# ---------------------------------------------------------------------------
+# Antialiased resampling (extension; the reading is written in the oracle).
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("shape", [(64, 80, 32, 40), (64, 80, 21, 33), (40, 30, 45, 17), (17, 23, 60, 70)])
+def test_aa_matches_torch_antialias(oracle, method, shape):
+    """torch's antialiased interpolate (PIL's filters, Keys a = -0.5 for
+    bicubic) is an independent implementation of the same definition."""
+    torch = pytest.importorskip("torch")
+    H, W, Ho, Wo = shape
+    x = np.random.default_rng(H * W).standard_normal((1, 2, H, W))
+    ref = oracle.resize_aa_nchw(x, Ho, Wo, method, -0.5)
+    t = torch.nn.functional.interpolate(torch.from_numpy(x), size=(Ho, Wo), mode={1: "bilinear", 2: "bicubic"}[method],
+                                        antialias=True, align_corners=False).numpy()
+    assert np.abs(ref - t).max() < 1e-12
+
+
+def test_aa_rows_sum_to_one_and_closed_form(oracle):
+    for n, m in ((100, 50), (97, 31), (30, 90), (64, 63)):
+        for method in (1, 2):
+            A = oracle.aa_axis_matrix(n, m, method)
+            assert np.abs(A.sum(1) - 1.0).max() < 1e-14
+    # triangle at x0.5: an interior output averages 4 samples with 1/8, 3/8, 3/8, 1/8
+    A = oracle.aa_axis_matrix(100, 50, 1)
+    j = 20
+    nz = np.nonzero(A[j])[0]
+    assert list(nz) == [2 * j - 1, 2 * j, 2 * j + 1, 2 * j + 2]
+    assert np.allclose(A[j, nz], [1 / 8, 3 / 8, 3 / 8, 1 / 8], atol=1e-15)
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_aa_upscale_is_half_pixel_interpolation_inside(oracle, method):
+    """Without a downscale the filter is not stretched: away from the
+    borders (no taps cut) antialiased resampling is half-pixel
+    interpolation."""
+    x = np.random.default_rng(3).standard_normal((40, 50, 1))
+    a = oracle.resize_aa(x, 100, 110, method)
+    b = oracle.resize(x, 100, 110, method, 1)
+    assert np.abs(a[10:-10, 10:-10] - b[10:-10, 10:-10]).max() < 1e-13
