@@ -96,6 +96,21 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
 typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_STREAM = 3,
                RS_IMPL_GATHER = 4, RS_IMPL_WINDOW = 5 } rs_impl;
 
+/* Option flags.
+ * RS_FLAG_ANTIALIAS - an extension beyond the paper's point sampling: the
+ *   bilinear (triangle) or bicubic (Keys, cubic_a) kernel is stretched by
+ *   the downscale factor f = max(n / m, 1) of each axis, so an output
+ *   averages the source footprint it covers: output j has centre
+ *   c = (j + 1/2) n / m, taps i = floor(c - R f + 1/2) .. floor(c + R f +
+ *   1/2) - 1 (R = 1 bilinear, 2 bicubic) cut to [0, n), weights
+ *   K((i + 1/2 - c) / f) renormalised to sum 1 (no edge replication; the
+ *   coord option does not apply). RS_F32 only, at most 8 taps per axis
+ *   (bilinear down to 1/4, bicubic down to 1/2), 16-byte source rows; one
+ *   fused pass (the register-window kernel with computed taps).
+ *   RS_ERR_UNSUPPORTED / RS_ERR_INVALID_ARG otherwise. Not for rs_resize,
+ *   the batch or the backward. */
+#define RS_FLAG_ANTIALIAS 1
+
 typedef struct {
     int32_t coord;      /* rs_coord; default RS_COORD_ASYMMETRIC */
     float cubic_a;      /* Keys parameter a for RS_BICUBIC; default -0.5 */
@@ -105,7 +120,7 @@ typedef struct {
     int32_t tile_h;     /* 0 = default. PLAIN: threads along y. TILED: output rows per tile. */
     int32_t threads;    /* 0 = default. TILED: threads per block (128 or 256). */
     int32_t waves;      /* 0 = default. STREAM: blocks per resident block slot. */
-    int32_t reserved;
+    int32_t flags;      /* RS_FLAG_* bits; 0 = none */
 } rs_options;
 
 /* Fills *opt with the defaults listed above. */

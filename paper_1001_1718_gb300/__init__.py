@@ -115,12 +115,14 @@ def _opts(coord, cubic_a, impl, tile, threads, waves=0) -> B.RsOptions:
 
 def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: str = "hwc",
            coord="asymmetric", cubic_a: float = -0.5, impl="auto", tile=None, threads: int = 0,
-           waves: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+           waves: int = 0, antialias: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
     """Resample x to size (Ho, Wo). Same dtype out; FP32 arithmetic.
 
     impl: "auto" (tuned or default kernel), "window", "stream", "tiled",
     "plain" or "gather" (nearest only);
-    tile = (tile_w, tile_h) and threads / waves override the kernel shape."""
+    tile = (tile_w, tile_h) and threads / waves override the kernel shape.
+    antialias: stretch the bilinear / bicubic kernel by the downscale factor
+    (FP32 only; see RS_FLAG_ANTIALIAS in include/resample.h)."""
     _require_cuda(x)
     Ho, Wo = int(size[0]), int(size[1])
     if out is None:
@@ -130,6 +132,8 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
         raise ValueError("out must have the dtype of x")
     Li, Lo = _layout(x, layout), _layout(out, layout)
     o = _opts(coord, cubic_a, impl, tile, threads, waves)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     with torch.cuda.device(x.device):
         B.check(lib().rs_resize_ex(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo),
                                    _dtype(x), _code(METHODS, method, "method"), ctypes.byref(o),

@@ -16,13 +16,14 @@ RS_U8, RS_F16, RS_BF16, RS_F32 = range(4)
 RS_NEAREST, RS_BILINEAR, RS_BICUBIC = range(3)
 RS_COORD_ASYMMETRIC, RS_COORD_HALF_PIXEL = range(2)
 RS_IMPL_AUTO, RS_IMPL_TILED, RS_IMPL_PLAIN, RS_IMPL_STREAM, RS_IMPL_GATHER, RS_IMPL_WINDOW = range(6)
+RS_FLAG_ANTIALIAS = 1
 RS_NOALLOC_MAX_IMAGES = 4096
 
 
 class RsOptions(ctypes.Structure):
     _fields_ = [("coord", ctypes.c_int32), ("cubic_a", ctypes.c_float), ("impl", ctypes.c_int32),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("waves", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("waves", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class RsLayout(ctypes.Structure):

@@ -369,12 +369,63 @@ k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const
 // each ascending), so the results equal the two-pass kernels'.
 struct AdjWinCfg {
     int band_h, band_cap, pos_cap, chunk, swe_max;
+    int aa_method;   // antialias taps (computed, not read from tables): M_BILINEAR / M_BICUBIC
+    float aa_a;      // Keys parameter of the antialias bicubic kernel
     size_t smem;
 };
+
+// Antialias taps of output j of an axis of m outputs over n samples (the
+// definition in rs_resize_ex's RS_FLAG_ANTIALIAS): the kernel stretched by
+// f = max(n / m, 1), taps cut to [0, n), weights renormalised. Ranges and
+// weights in FP64 (so the ranges match the host's exactly), weights then
+// rounded to FP32.
+__device__ __forceinline__ void aa_range(int j, int n, int m, int method, int& lo, int& hi)
+{
+    const double R = method == M_BILINEAR ? 1.0 : 2.0;
+    const double f = fmax((double)n / m, 1.0);
+    const double c = (j + 0.5) * n / m;
+    lo = max((int)floor(c - R * f + 0.5), 0);
+    hi = min((int)floor(c + R * f + 0.5), n);   // exclusive
+}
+
+template <int K>
+__device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a, int& lo, float* w,
+                                        unsigned int* fault)
+{
+    int hi;
+    aa_range(j, n, m, method, lo, hi);
+    int cnt = max(0, hi - lo);
+    if (cnt > K) {   // excluded by the host
+        report_fault(fault, FAULT_BWD_TAPS);
+        cnt = K;
+    }
+    const double f = fmax((double)n / m, 1.0);
+    const double c = (j + 0.5) * n / m;
+    const double ad = a;
+    double ww[K];
+    double tot = 0.0;
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+        if (k < cnt) {
+            const double u = fabs((lo + k + 0.5 - c) / f);
+            if (method == M_BILINEAR) v = fmax(0.0, 1.0 - u);
+            else if (u <= 1.0) v = ((ad + 2.0) * u - (ad + 3.0)) * u * u + 1.0;
+            else if (u < 2.0) v = ((ad * u - 5.0 * ad) * u + 8.0 * ad) * u - 4.0 * ad;
+        }
+        ww[k] = v;
+        tot += v;
+    }
+    #pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = (float)(tot != 0.0 ? ww[k] / tot : ww[k]);
+}
 static constexpr int kAwThreads = 256;
 static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
 
-template <int C, int KX, int KY>
+// AA: the same pass with antialias taps computed from the definition
+// instead of read from the transposed tables (the "dY" rows are then the
+// source image and the "dX" rows the output).
+template <int C, int KX, int KY, bool AA>
 __global__ void __launch_bounds__(kAwThreads, 2)
 k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, const AdjTables tb,
              const AdjWinCfg cfg, unsigned int* fault)
@@ -393,8 +444,17 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     // dY columns under the strip: [a0, c_hi), a0 on a 16-byte boundary; the
     // columns past the row (x taps beyond a range, zero weights) read zeros.
     const int x_first = e0 / C, x_last = (e0 + nE - 1) / C;
-    const int a0 = (__ldg(tb.xlo + x_first) * C) & ~3;
-    const int c_hi = (__ldg(tb.xlo + x_last) + KX) * C;
+    auto xlo_of = [&](int x) {
+        if constexpr (AA) {
+            int lo, hi;
+            aa_range(x, g.Wo, g.W, cfg.aa_method, lo, hi);
+            return lo;
+        } else {
+            return __ldg(tb.xlo + x);
+        }
+    };
+    const int a0 = (xlo_of(x_first) * C) & ~3;
+    const int c_hi = (xlo_of(x_last) + KX) * C;
     const int in_hi = min(c_hi, WoC);
     const int units = (in_hi - a0 + 3) / 4;
     const int R = cfg.chunk;
@@ -415,10 +475,17 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     }
     for (int i = tid; i < nrows; i += kAwThreads) {
         const int r = yb + i;
-        RF[i] = __ldg(tb.ylo + r);
-        const int cnt = __ldg(tb.ycnt + r);
-        #pragma unroll
-        for (int p = 0; p < KY; ++p) RW[i * KY + p] = p < cnt ? __ldg(tb.yw + (int64_t)r * tb.yK + p) : 0.0f;
+        if constexpr (AA) {
+            float w[KY];
+            aa_taps<KY>(r, g.Ho, g.H, cfg.aa_method, cfg.aa_a, RF[i], w, fault);
+            #pragma unroll
+            for (int p = 0; p < KY; ++p) RW[i * KY + p] = w[p];
+        } else {
+            RF[i] = __ldg(tb.ylo + r);
+            const int cnt = __ldg(tb.ycnt + r);
+            #pragma unroll
+            for (int p = 0; p < KY; ++p) RW[i * KY + p] = p < cnt ? __ldg(tb.yw + (int64_t)r * tb.yK + p) : 0.0f;
+        }
     }
     // x taps of this thread's two elements, paired for FP32x2
     int off[2];
@@ -430,10 +497,16 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
             const int el = tid + kAwThreads * k;
             if (el < nE) {
                 const int e = e0 + el, x = e / C, c = e - x * C;
-                const int lo = __ldg(tb.xlo + x), cnt = __ldg(tb.xcnt + x);
+                int lo;
+                if constexpr (AA) {
+                    aa_taps<KX>(x, g.Wo, g.W, cfg.aa_method, cfg.aa_a, lo, wx[k], fault);
+                } else {
+                    lo = __ldg(tb.xlo + x);
+                    const int cnt = __ldg(tb.xcnt + x);
+                    #pragma unroll
+                    for (int q = 0; q < KX; ++q) wx[k][q] = q < cnt ? __ldg(tb.xw + (int64_t)x * tb.xK + q) : 0.0f;
+                }
                 off[k] = lo * C + c - a0;
-                #pragma unroll
-                for (int q = 0; q < KX; ++q) wx[k][q] = q < cnt ? __ldg(tb.xw + (int64_t)x * tb.xK + q) : 0.0f;
             } else {
                 off[k] = 0;
                 #pragma unroll
@@ -635,26 +708,31 @@ static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, A
 }
 
 template <int C, int KX, int KY>
-static void* adj_window_func() { return reinterpret_cast<void*>(&k_adj_window<C, KX, KY>); }
+static void* adj_window_func(bool aa)
+{
+    return aa ? reinterpret_cast<void*>(&k_adj_window<C, KX, KY, true>)
+              : reinterpret_cast<void*>(&k_adj_window<C, KX, KY, false>);
+}
 
 template <int C, int KX>
-static void* adj_window_fy(int KY)
+static void* adj_window_fy(int KY, bool aa)
 {
-    return KY == 2 ? adj_window_func<C, KX, 2>() : KY == 4 ? adj_window_func<C, KX, 4>() : adj_window_func<C, KX, 8>();
+    return KY == 2 ? adj_window_func<C, KX, 2>(aa) : KY == 4 ? adj_window_func<C, KX, 4>(aa)
+                                                           : adj_window_func<C, KX, 8>(aa);
 }
 
 template <int C>
-static void* adj_window_fx(int KX, int KY)
+static void* adj_window_fx(int KX, int KY, bool aa)
 {
-    return KX == 2 ? adj_window_fy<C, 2>(KY) : KX == 4 ? adj_window_fy<C, 4>(KY) : adj_window_fy<C, 8>(KY);
+    return KX == 2 ? adj_window_fy<C, 2>(KY, aa) : KX == 4 ? adj_window_fy<C, 4>(KY, aa) : adj_window_fy<C, 8>(KY, aa);
 }
 
 static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const float* dY, float* dX, const AdjTables& tb,
-                                     AdjWinCfg c, cudaStream_t st)
+                                     AdjWinCfg c, cudaStream_t st, bool aa = false)
 {
     const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
-    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY) : g.C == 2 ? adj_window_fx<2>(KX, KY)
-               : g.C == 3 ? adj_window_fx<3>(KX, KY) : adj_window_fx<4>(KX, KY);
+    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, aa) : g.C == 2 ? adj_window_fx<2>(KX, KY, aa)
+               : g.C == 3 ? adj_window_fx<3>(KX, KY, aa) : adj_window_fx<4>(KX, KY, aa);
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
@@ -669,6 +747,50 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
     void* args[] = {const_cast<Geom*>(&g), const_cast<float**>(&dY), &dX, const_cast<AdjTables*>(&tb), &c, &fw};
     e = cudaLaunchKernel(func, grid, dim3(kAwThreads), args, c.smem, st);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Host ranges of the antialias taps (same FP64 formula as aa_range).
+static AxisRanges aa_ranges(int n, int m, int method)
+{
+    AxisRanges R;
+    R.lo.resize(m);
+    R.hi.resize(m);
+    const double Rk = method == M_BILINEAR ? 1.0 : 2.0;
+    const double f = std::max((double)n / m, 1.0);
+    for (int j = 0; j < m; ++j) {
+        const double c = (j + 0.5) * n / m;
+        const int lo = std::max((int)std::floor(c - Rk * f + 0.5), 0);
+        const int hi = std::min((int)std::floor(c + Rk * f + 0.5), n);
+        R.lo[j] = lo;
+        R.hi[j] = hi - 1;
+        R.kmax = std::max(R.kmax, hi - lo);
+    }
+    return R;
+}
+
+rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* src, void* dst, const rs_options& o,
+                           cudaStream_t st)
+{
+    if (dtype != DT_F32) return RS_ERR_UNSUPPORTED;
+    if (method != M_BILINEAR && method != M_BICUBIC) return RS_ERR_INVALID_ARG;
+    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) return RS_ERR_INVALID_ARG;
+    // The fused window pass in its adjoint roles: "dY" (Ho x Wo there) is the
+    // source image, "dX" (H x W) the output.
+    Geom g = gf;
+    g.H = gf.Ho; g.W = gf.Wo; g.Ho = gf.H; g.Wo = gf.W;
+    g.sp = gf.dp; g.dp = gf.sp;
+    g.src_pitch = gf.dst_pitch; g.dst_pitch = gf.src_pitch;
+    BwdPlan p;
+    p.ry = aa_ranges(gf.H, gf.Ho, method);
+    p.rx = aa_ranges(gf.W, gf.Wo, method);
+    p.yK = std::max(1, p.ry.kmax);
+    p.xK = std::max(1, p.rx.kmax);
+    AdjWinCfg c;
+    if (!adj_window_config(g, p, src, c)) return RS_ERR_UNSUPPORTED;
+    c.aa_method = method;
+    c.aa_a = o.cubic_a;
+    return cuda_status(launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst), AdjTables{},
+                                         c, st, true));
 }
 
 template <int KX, int C>
@@ -730,6 +852,7 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
 {
     if (dtype != RS_F32) return RS_ERR_UNSUPPORTED;
     const rs_options o = options_or_default(opt);
+    if (o.flags) return RS_ERR_INVALID_ARG;   // no antialiased backward
     Geom g;
     // make_geom checks pointers, alignment and overlap with src = dX, dst = dY.
     rs_status s = make_geom(grad_in, in, grad_out, out, RS_F32, method, o, g);

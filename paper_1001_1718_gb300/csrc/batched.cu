@@ -313,6 +313,7 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
     if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
     rs_status s = check_options(o, RS_BILINEAR);
     if (s != RS_OK) return s;
+    if (o.flags) return RS_ERR_INVALID_ARG;   // no antialiased batch
     BatchShape sh;
     if ((s = batch_shape(d, n, dtype, o, tuned, sh)) != RS_OK) return s;
     const bool window_opts = o.impl == RS_IMPL_WINDOW;   // tile_w / tile_h describe the window items

@@ -32,6 +32,7 @@ rs_status check_options(const rs_options& o, int method)
     if (!std::isfinite(o.cubic_a)) return RS_ERR_INVALID_ARG;
     if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_WINDOW) return RS_ERR_INVALID_ARG;
     if (o.tile_w < 0 || o.tile_h < 0 || o.threads < 0 || o.waves < 0) return RS_ERR_INVALID_ARG;
+    if (o.flags & ~RS_FLAG_ANTIALIAS) return RS_ERR_INVALID_ARG;
     if (method < RS_NEAREST || method > RS_BICUBIC) return RS_ERR_INVALID_ARG;
     return RS_OK;
 }
@@ -172,6 +173,7 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst, const rs
     rs_status s = make_geom(src, in, dst, out, dtype, method, o, g);
     if (s != RS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (o.flags & RS_FLAG_ANTIALIAS) return resize_antialias(g, method, dtype, src, dst, o, st);
     if (o.impl == RS_IMPL_PLAIN) {
         const int bw = o.tile_w ? o.tile_w : 32, bh = o.tile_h ? o.tile_h : 4;
         if (bw * bh > 1024 || bw < 1 || bh < 1 || bh > 64) return RS_ERR_INVALID_ARG;

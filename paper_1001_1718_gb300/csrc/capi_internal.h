@@ -40,6 +40,11 @@ cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src,
 
 cudaError_t read_fault(cudaStream_t st, unsigned int* code);
 
+// RS_FLAG_ANTIALIAS forward (backward.cu: the fused window pass with
+// computed taps).
+rs_status resize_antialias(const Geom& g, int method, int dtype, const void* src, void* dst, const rs_options& o,
+                           cudaStream_t st);
+
 // Tuning cache entry: kernel (rs_impl) and shape; see autotune.cpp.
 struct Tuned {
     int impl, tile_w, tile_h, threads, waves;

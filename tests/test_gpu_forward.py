@@ -304,3 +304,39 @@ def test_window_shifted_staging(rs, oracle, dtype):
     torch.cuda.synchronize()
     check(y, oracle.resize(x64, 190, 400, BC, 0), dtype, BC, np.abs(x64).max(), f"shifted view {dtype}")
     assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("method", [BL, BC])
+def test_antialias_matches_oracle(rs, oracle, method):
+    """RS_FLAG_ANTIALIAS (the kernel stretched by the downscale factor, taps
+    cut to the image and renormalised) against the FP64 oracle: FP32 NCHW
+    and interleaved, down- and upscales, ragged strips."""
+    for k, (N, C, H, W, Ho, Wo) in enumerate([(2, 3, 64, 80, 32, 40), (1, 2, 97, 132, 49, 67),
+                                               (1, 1, 300, 520, 170, 300), (2, 1, 40, 36, 90, 72)]):
+        if method == BC and (H / Ho > 2 or W / Wo > 2):
+            continue
+        x = np.random.default_rng(1400 + k).standard_normal((N, C, H, W)).astype(np.float32)
+        y = rs.resize(torch.from_numpy(x).cuda(), (Ho, Wo), MNAME[method], layout="nchw", antialias=True)
+        torch.cuda.synchronize()
+        ref = oracle.resize_aa_nchw(x.astype(np.float64), Ho, Wo, method)
+        check(y, ref, "f32", method, float(np.abs(x).max()), f"antialias nchw {MNAME[method]} {(N, C, H, W)}->{Ho}x{Wo}")
+    # interleaved channels; bilinear down to 1/4
+    x = np.random.default_rng(1500).standard_normal((256, 200, 3)).astype(np.float32)
+    for (Ho, Wo) in ((128, 100), (64, 52), (130, 101)):
+        if method == BC and (256 / Ho > 2 or 200 / Wo > 2):
+            continue
+        y = rs.resize(torch.from_numpy(x).cuda(), (Ho, Wo), MNAME[method], antialias=True)
+        torch.cuda.synchronize()
+        check(y, oracle.resize_aa(x.astype(np.float64), Ho, Wo, method), "f32", method, float(np.abs(x).max()),
+              f"antialias hwc {MNAME[method]} -> {Ho}x{Wo}")
+    assert rs.debug_fault() == 0
+
+
+def test_antialias_refusals(rs):
+    xf = torch.randn(64, 64, device="cuda")
+    with pytest.raises(rs.ResampleError):          # more than 8 taps: bicubic below 1/2
+        rs.resize(xf, (20, 20), "bicubic", antialias=True)
+    with pytest.raises(rs.ResampleError):          # nearest has no filter to stretch
+        rs.resize(xf, (32, 32), "nearest", antialias=True)
+    with pytest.raises(rs.ResampleError):          # FP32 only
+        rs.resize(torch.zeros(64, 64, dtype=torch.uint8, device="cuda"), (32, 32), "bilinear", antialias=True)
