@@ -562,6 +562,12 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak):
             ref = oracle.adjoint(gp, 512, 512, rs.METHODS[method])[:, :, 0]
             rec(f"nchw_f32_{method}_x{s:g}_bwd", ms, y.numel() * 4, xn.numel() * 4, 96 * 512 * 512,
                 max_abs_vs_f64_adjoint_plane0=float(np.abs(gi[0, 0].cpu().numpy() - ref).max()))
+            if s < 1:   # antialiased downscale (the filter stretched by the factor)
+                ms = bench(lambda: rs.resize(xn, (Ho, Wo), method, layout="nchw", out=y, antialias=True), 10)
+                ref = oracle.resize_aa(xn[0, 0].cpu().numpy().astype(np.float64), Ho, Wo,
+                                       rs.METHODS[method])[:, :, 0]
+                rec(f"nchw_f32_{method}_x{s:g}_fwd_antialias", ms, xn.numel() * 4, y.numel() * 4, 96 * Ho * Wo,
+                    max_abs_vs_f64_plane0=float(np.abs(y[0, 0].cpu().numpy() - ref).max()))
             del y, g, gi, ws
     del xn
     torch.cuda.empty_cache()
