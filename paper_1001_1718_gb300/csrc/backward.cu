@@ -376,16 +376,28 @@ struct AdjWinCfg {
 
 // Antialias taps of output j of an axis of m outputs over n samples (the
 // definition in rs_resize_ex's RS_FLAG_ANTIALIAS): the kernel stretched by
-// f = max(n / m, 1), taps cut to [0, n), weights renormalised. Ranges and
-// weights in FP64 (so the ranges match the host's exactly), weights then
-// rounded to FP32.
-__device__ __forceinline__ void aa_range(int j, int n, int m, int method, int& lo, int& hi)
+// f = max(n / m, 1), taps cut to [0, n), weights renormalised. In exact
+// integer arithmetic with F = max(n, m) = m f: the centre is
+// c = (2j + 1) n / (2m), so the taps run from floor(((2j+1) n - 2 R F + m) /
+// (2m)) to floor(((2j+1) n + 2 R F + m) / (2m)) - 1, and tap i sits at
+// u = ((2i+1) m - (2j+1) n) / (2F) kernel units. (Where that bound is an
+// exact integer an FP64 evaluation may add or drop the boundary tap; its
+// weight K(+-R) is zero.) The weights are evaluated in FP32.
+__host__ __device__ inline int64_t floor_div_i64(int64_t a, int64_t b)   // b > 0
 {
-    const double R = method == M_BILINEAR ? 1.0 : 2.0;
-    const double f = fmax((double)n / m, 1.0);
-    const double c = (j + 0.5) * n / m;
-    lo = max((int)floor(c - R * f + 0.5), 0);
-    hi = min((int)floor(c + R * f + 0.5), n);   // exclusive
+    const int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+__host__ __device__ inline void aa_range(int j, int n, int m, int method, int& lo, int& hi)
+{
+    const int64_t R = method == M_BILINEAR ? 1 : 2;
+    const int64_t F = n > m ? n : m;
+    const int64_t a = (int64_t)(2 * j + 1) * n + m;
+    const int64_t l = floor_div_i64(a - 2 * R * F, 2 * (int64_t)m);
+    const int64_t h = floor_div_i64(a + 2 * R * F, 2 * (int64_t)m);
+    lo = (int)(l < 0 ? 0 : l);
+    hi = (int)(h > n ? n : h);   // exclusive
 }
 
 template <int K>
@@ -399,25 +411,24 @@ __device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a
         report_fault(fault, FAULT_BWD_TAPS);
         cnt = K;
     }
-    const double f = fmax((double)n / m, 1.0);
-    const double c = (j + 0.5) * n / m;
-    const double ad = a;
-    double ww[K];
-    double tot = 0.0;
+    const float inv2F = 1.0f / (2.0f * (float)max(n, m));
+    const int64_t cj = (int64_t)(2 * j + 1) * n;
+    float tot = 0.0f;
     #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double v = 0.0;
+        float v = 0.0f;
         if (k < cnt) {
-            const double u = fabs((lo + k + 0.5 - c) / f);
-            if (method == M_BILINEAR) v = fmax(0.0, 1.0 - u);
-            else if (u <= 1.0) v = ((ad + 2.0) * u - (ad + 3.0)) * u * u + 1.0;
-            else if (u < 2.0) v = ((ad * u - 5.0 * ad) * u + 8.0 * ad) * u - 4.0 * ad;
+            const float u = fabsf((float)((int64_t)(2 * (lo + k) + 1) * m - cj) * inv2F);
+            if (method == M_BILINEAR) v = fmaxf(0.0f, 1.0f - u);
+            else if (u <= 1.0f) v = ((a + 2.0f) * u - (a + 3.0f)) * u * u + 1.0f;
+            else if (u < 2.0f) v = ((a * u - 5.0f * a) * u + 8.0f * a) * u - 4.0f * a;
         }
-        ww[k] = v;
+        w[k] = v;
         tot += v;
     }
+    const float inv = tot != 0.0f ? 1.0f / tot : 1.0f;
     #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = (float)(tot != 0.0 ? ww[k] / tot : ww[k]);
+    for (int k = 0; k < K; ++k) w[k] *= inv;
 }
 static constexpr int kAwThreads = 256;
 static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
@@ -749,18 +760,15 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Host ranges of the antialias taps (same FP64 formula as aa_range).
+// Host ranges of the antialias taps (the same integer bounds as the kernel).
 static AxisRanges aa_ranges(int n, int m, int method)
 {
     AxisRanges R;
     R.lo.resize(m);
     R.hi.resize(m);
-    const double Rk = method == M_BILINEAR ? 1.0 : 2.0;
-    const double f = std::max((double)n / m, 1.0);
     for (int j = 0; j < m; ++j) {
-        const double c = (j + 0.5) * n / m;
-        const int lo = std::max((int)std::floor(c - Rk * f + 0.5), 0);
-        const int hi = std::min((int)std::floor(c + Rk * f + 0.5), n);
+        int lo, hi;
+        aa_range(j, n, m, method, lo, hi);
         R.lo[j] = lo;
         R.hi[j] = hi - 1;
         R.kmax = std::max(R.kmax, hi - lo);
