@@ -62,8 +62,10 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
 
 /* Kernel selection.
  * AUTO   = the tuned (or default) kernel for the problem: GATHER for
- *          RS_NEAREST; WINDOW for bilinear / bicubic when its footprint fits
- *          in shared memory, else STREAM, else TILED.
+ *          RS_NEAREST; for bilinear / bicubic REDUCE on RS_F32 vertical
+ *          downscales to at least 1/4 (outputs >= 2^20 elements), WINDOW on
+ *          large vertical upscales and uint8 outputs, where its footprint
+ *          fits in shared memory; else STREAM, else TILED.
  * WINDOW = bilinear / bicubic: each thread owns 4 output elements (strided
  *          by 256) of a 1024-element strip for a whole band of rows and keeps the
  *          horizontally interpolated source rows its taps need in registers,
@@ -90,11 +92,24 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
  *          Otherwise each thread copies 16 bytes of a strip of tile_w output
  *          elements over tile_h consecutive output rows, reusing a gathered
  *          row for the next output row when both map to the same source row.
+ * REDUCE = RS_F32 bilinear / bicubic with source rows of whole aligned
+ *          16-byte units (pointer, pitch and W*C multiples of 4 elements):
+ *          the register window in its transposed roles (the backward's fused
+ *          kernel with the taps of Eqs. 1-5 computed in the kernel). Each
+ *          thread owns 2 output elements (strided by 256) of a 512-element
+ *          strip for a band of output rows; the source rows the band's taps
+ *          reach are copied with 16-byte cp.async into a three-slot ring and
+ *          horizontally interpolated at the thread's columns into a register
+ *          window; every output row whose first tap is the window's first
+ *          row is blended from registers. Taps that clamp onto the same
+ *          edge column are merged (their weights summed), so sums at the
+ *          left and right edges may round differently from the other
+ *          kernels. Any scale; tile_w / tile_h / threads / waves must be 0.
  * PLAIN  = one thread per output pixel reading its taps from global memory,
  *          thread blocks of tile_w x tile_h threads (default 32 x 4): the
  *          paper's kernel (Sec. III.A, Eq. 6), kept as the comparison row. */
 typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_STREAM = 3,
-               RS_IMPL_GATHER = 4, RS_IMPL_WINDOW = 5 } rs_impl;
+               RS_IMPL_GATHER = 4, RS_IMPL_WINDOW = 5, RS_IMPL_REDUCE = 6 } rs_impl;
 
 /* Option flags.
  * RS_FLAG_ANTIALIAS - an extension beyond the paper's point sampling: the

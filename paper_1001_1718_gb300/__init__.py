@@ -23,7 +23,8 @@ from ._binding import ResampleError, lib
 METHODS = {"nearest": B.RS_NEAREST, "bilinear": B.RS_BILINEAR, "bicubic": B.RS_BICUBIC}
 COORDS = {"asymmetric": B.RS_COORD_ASYMMETRIC, "half_pixel": B.RS_COORD_HALF_PIXEL}
 IMPLS = {"auto": B.RS_IMPL_AUTO, "tiled": B.RS_IMPL_TILED, "plain": B.RS_IMPL_PLAIN,
-         "stream": B.RS_IMPL_STREAM, "gather": B.RS_IMPL_GATHER, "window": B.RS_IMPL_WINDOW}
+         "stream": B.RS_IMPL_STREAM, "gather": B.RS_IMPL_GATHER, "window": B.RS_IMPL_WINDOW,
+         "reduce": B.RS_IMPL_REDUCE}
 IMPL_NAMES = {v: k for k, v in IMPLS.items()}
 DTYPES = {torch.uint8: B.RS_U8, torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16,
           torch.float32: B.RS_F32}
@@ -118,8 +119,8 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
            waves: int = 0, antialias: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
     """Resample x to size (Ho, Wo). Same dtype out; FP32 arithmetic.
 
-    impl: "auto" (tuned or default kernel), "window", "stream", "tiled",
-    "plain" or "gather" (nearest only);
+    impl: "auto" (tuned or default kernel), "window", "reduce" (FP32),
+    "stream", "tiled", "plain" or "gather" (nearest only);
     tile = (tile_w, tile_h) and threads / waves override the kernel shape.
     antialias: stretch the bilinear / bicubic kernel by the downscale factor
     (FP32 only; see RS_FLAG_ANTIALIAS in include/resample.h)."""

@@ -61,6 +61,7 @@ static bool valid_tuned(const Tuned& t)
     if (t.impl == RS_IMPL_WINDOW) return t.tile_h >= 0 && t.tile_w > 0 && (t.waves > 0 || t.tile_w <= 256);
     if (t.impl == RS_IMPL_STREAM) return t.tile_w > 0 && t.tile_h > 0 && t.waves > 0;
     if (t.impl == RS_IMPL_TILED) return t.tile_w > 0 && t.tile_h > 0 && (t.threads == 128 || t.threads == 256);
+    if (t.impl == RS_IMPL_REDUCE) return true;
     return false;
 }
 
@@ -108,6 +109,7 @@ static bool make_choice(const Geom& g, int method, int dtype, const void* src, c
         k.window.waves = t.waves;
         return poly_config(g, method, dtype, src, k.window);
     }
+    if (t.impl == RS_IMPL_REDUCE) return reduce_config(g, method, dtype, src, nullptr);
     if (t.impl == RS_IMPL_STREAM) {
         k.stream = StreamCfg{};
         k.stream.tile_w = t.tile_w;
@@ -133,6 +135,15 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
     // for FP32): 8-row chunks when they leave room for three blocks per SM,
     // else 4-row chunks, within ~100 KB.
     const int64_t out_elems = (int64_t)g.Ho * g.Wo * g.C * g.planes;
+    // FP32 vertical downscales to at least 1/4 (every source row feeds an
+    // output row): the window pass in its transposed roles, within ~100 KB.
+    if (dtype == DT_F32 && g.Ho < g.H && 4 * (int64_t)g.Ho >= g.H && out_elems >= (int64_t)1 << 20) {
+        size_t smem = 0;
+        if (reduce_config(g, method, dtype, src, &smem) && smem <= 100 * 1024) {
+            k.impl = RS_IMPL_REDUCE;
+            return true;
+        }
+    }
     if ((g.Ho >= g.H || dtype == DT_U8) && out_elems >= (int64_t)1 << 22) {
         for (int ch : {8, 4}) {
             const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
@@ -164,6 +175,11 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
     }
     if (o.impl == RS_IMPL_WINDOW) {
         const Tuned t{RS_IMPL_WINDOW, 1024, o.tile_h ? o.tile_h : 8, 256, o.waves ? o.waves : 2};
+        return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
+    }
+    if (o.impl == RS_IMPL_REDUCE) {
+        if (explicit_shape) return RS_ERR_INVALID_ARG;
+        const Tuned t{RS_IMPL_REDUCE, 0, 0, 256, 0};
         return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
     }
     if (o.impl == RS_IMPL_STREAM || (o.impl == RS_IMPL_AUTO && explicit_shape && !o.threads)) {
@@ -198,6 +214,7 @@ cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src,
     if (k.impl == RS_IMPL_GATHER) return launch_nearest(g, dtype, src, dst, k.gather_w, k.gather_rows, st);
     if (k.impl == RS_IMPL_WINDOW) return launch_poly(g, method, dtype, src, dst, k.window, st);
     if (k.impl == RS_IMPL_STREAM) return launch_stream(g, method, dtype, src, dst, k.stream, st);
+    if (k.impl == RS_IMPL_REDUCE) return launch_reduce(g, method, dtype, src, dst, st);
     return launch_tiled(g, method, dtype, src, dst, k.tile, st);
 }
 
@@ -234,6 +251,7 @@ static Tuned to_tuned(const KernelChoice& k)
     if (k.impl == RS_IMPL_GATHER) return Tuned{RS_IMPL_GATHER, k.gather_w, k.gather_rows, 256, 0};
     if (k.impl == RS_IMPL_WINDOW) return Tuned{RS_IMPL_WINDOW, 1024, k.window.chunk, 256, k.window.waves};
     if (k.impl == RS_IMPL_STREAM) return Tuned{RS_IMPL_STREAM, k.stream.tile_w, k.stream.chunk_h, 256, k.stream.waves};
+    if (k.impl == RS_IMPL_REDUCE) return Tuned{RS_IMPL_REDUCE, 0, 0, 256, 0};
     return Tuned{RS_IMPL_TILED, k.tile.tile_w, k.tile.tile_h, k.tile.threads, 0};
 }
 
@@ -261,6 +279,7 @@ rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_
     if (s != RS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<Tuned> cands;
+    cands.push_back(Tuned{RS_IMPL_REDUCE, 0, 0, 256, 0});
     for (int ch : {4, 8, 16})
         for (int wv : {1, 2, 4}) cands.push_back(Tuned{RS_IMPL_WINDOW, 1024, ch, 256, wv});
     for (int tw : {128, 256, 512, 1024})

@@ -369,8 +369,8 @@ k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const
 // each ascending), so the results equal the two-pass kernels'.
 struct AdjWinCfg {
     int band_h, band_cap, pos_cap, chunk, swe_max;
-    int aa_method;   // antialias taps (computed, not read from tables): M_BILINEAR / M_BICUBIC
-    float aa_a;      // Keys parameter of the antialias bicubic kernel
+    int tap_method;  // computed taps (TAPS_AA, TAPS_POINT): M_BILINEAR / M_BICUBIC
+    float tap_a;     // Keys parameter of the bicubic kernel
     size_t smem;
 };
 
@@ -433,10 +433,17 @@ __device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a
 static constexpr int kAwThreads = 256;
 static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
 
-// AA: the same pass with antialias taps computed from the definition
-// instead of read from the transposed tables (the "dY" rows are then the
-// source image and the "dX" rows the output).
-template <int C, int KX, int KY, bool AA>
+// Where the taps come from. TAPS_TABLE: the transposed tables of the
+// adjoint. TAPS_AA / TAPS_POINT: the same pass as a forward resampling, the
+// "dY" rows being the source image and the "dX" rows the output, with the
+// taps computed from the definition: antialias taps (the stretched kernel),
+// or the point-sampled taps of Eqs. 1-5. Point taps keep the rows' clamped
+// virtual indices (the staging clamps rows) and, along x, merge the weights
+// of taps that clamp onto the same column, so that every output reads KX
+// consecutive staged columns from max(first tap, 0).
+enum { TAPS_TABLE = 0, TAPS_AA = 1, TAPS_POINT = 2 };
+
+template <int C, int KX, int KY, int TM>
 __global__ void __launch_bounds__(kAwThreads, 2)
 k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, const AdjTables tb,
              const AdjWinCfg cfg, unsigned int* fault)
@@ -456,10 +463,12 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     // columns past the row (x taps beyond a range, zero weights) read zeros.
     const int x_first = e0 / C, x_last = (e0 + nE - 1) / C;
     auto xlo_of = [&](int x) {
-        if constexpr (AA) {
+        if constexpr (TM == TAPS_AA) {
             int lo, hi;
-            aa_range(x, g.Wo, g.W, cfg.aa_method, lo, hi);
+            aa_range(x, g.Wo, g.W, cfg.tap_method, lo, hi);
             return lo;
+        } else if constexpr (TM == TAPS_POINT) {
+            return max(first_tap<KX>(x, g.Wo, g.W, g.coord), 0);
         } else {
             return __ldg(tb.xlo + x);
         }
@@ -486,9 +495,14 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     }
     for (int i = tid; i < nrows; i += kAwThreads) {
         const int r = yb + i;
-        if constexpr (AA) {
+        if constexpr (TM == TAPS_AA) {
             float w[KY];
-            aa_taps<KY>(r, g.Ho, g.H, cfg.aa_method, cfg.aa_a, RF[i], w, fault);
+            aa_taps<KY>(r, g.Ho, g.H, cfg.tap_method, cfg.tap_a, RF[i], w, fault);
+            #pragma unroll
+            for (int p = 0; p < KY; ++p) RW[i * KY + p] = w[p];
+        } else if constexpr (TM == TAPS_POINT) {
+            float w[KY];
+            RF[i] = taps<KY>(r, g.Ho, g.H, g.coord, cfg.tap_a, w);
             #pragma unroll
             for (int p = 0; p < KY; ++p) RW[i * KY + p] = w[p];
         } else {
@@ -509,8 +523,20 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
             if (el < nE) {
                 const int e = e0 + el, x = e / C, c = e - x * C;
                 int lo;
-                if constexpr (AA) {
-                    aa_taps<KX>(x, g.Wo, g.W, cfg.aa_method, cfg.aa_a, lo, wx[k], fault);
+                if constexpr (TM == TAPS_AA) {
+                    aa_taps<KX>(x, g.Wo, g.W, cfg.tap_method, cfg.tap_a, lo, wx[k], fault);
+                } else if constexpr (TM == TAPS_POINT) {
+                    float wt[KX];
+                    const int f = taps<KX>(x, g.Wo, g.W, g.coord, cfg.tap_a, wt);
+                    lo = max(f, 0);
+                    #pragma unroll
+                    for (int q = 0; q < KX; ++q) wx[k][q] = 0.0f;
+                    #pragma unroll
+                    for (int q = 0; q < KX; ++q) {   // tap q lands on column lo + dq
+                        const int dq = clampi(f + q, g.Wo) - lo;
+                        #pragma unroll
+                        for (int t = 0; t < KX; ++t) wx[k][t] += dq == t ? wt[q] : 0.0f;
+                    }
                 } else {
                     lo = __ldg(tb.xlo + x);
                     const int cnt = __ldg(tb.xcnt + x);
@@ -719,31 +745,35 @@ static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, A
 }
 
 template <int C, int KX, int KY>
-static void* adj_window_func(bool aa)
+static void* adj_window_func(int tm)
 {
-    return aa ? reinterpret_cast<void*>(&k_adj_window<C, KX, KY, true>)
-              : reinterpret_cast<void*>(&k_adj_window<C, KX, KY, false>);
+    return tm == TAPS_AA ? reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_AA>)
+                         : reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_TABLE>);
 }
 
 template <int C, int KX>
-static void* adj_window_fy(int KY, bool aa)
+static void* adj_window_fy(int KY, int tm)
 {
-    return KY == 2 ? adj_window_func<C, KX, 2>(aa) : KY == 4 ? adj_window_func<C, KX, 4>(aa)
-                                                           : adj_window_func<C, KX, 8>(aa);
+    return KY == 2 ? adj_window_func<C, KX, 2>(tm) : KY == 4 ? adj_window_func<C, KX, 4>(tm)
+                                                           : adj_window_func<C, KX, 8>(tm);
 }
 
 template <int C>
-static void* adj_window_fx(int KX, int KY, bool aa)
+static void* adj_window_fx(int KX, int KY, int tm)
 {
-    return KX == 2 ? adj_window_fy<C, 2>(KY, aa) : KX == 4 ? adj_window_fy<C, 4>(KY, aa) : adj_window_fy<C, 8>(KY, aa);
+    if (tm == TAPS_POINT)   // the method's own taps on both axes: KX == KY in {2, 4}
+        return KX == 2 ? reinterpret_cast<void*>(&k_adj_window<C, 2, 2, TAPS_POINT>)
+                       : reinterpret_cast<void*>(&k_adj_window<C, 4, 4, TAPS_POINT>);
+    return KX == 2 ? adj_window_fy<C, 2>(KY, tm) : KX == 4 ? adj_window_fy<C, 4>(KY, tm) : adj_window_fy<C, 8>(KY, tm);
 }
 
 static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const float* dY, float* dX, const AdjTables& tb,
-                                     AdjWinCfg c, cudaStream_t st, bool aa = false)
+                                     AdjWinCfg c, cudaStream_t st, int tm = TAPS_TABLE)
 {
     const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
-    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, aa) : g.C == 2 ? adj_window_fx<2>(KX, KY, aa)
-               : g.C == 3 ? adj_window_fx<3>(KX, KY, aa) : adj_window_fx<4>(KX, KY, aa);
+    if (tm == TAPS_POINT && (KX != KY || KX > 4)) return cudaErrorInvalidValue;
+    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, tm) : g.C == 2 ? adj_window_fx<2>(KX, KY, tm)
+               : g.C == 3 ? adj_window_fx<3>(KX, KY, tm) : adj_window_fx<4>(KX, KY, tm);
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
@@ -795,10 +825,67 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
     p.xK = std::max(1, p.rx.kmax);
     AdjWinCfg c;
     if (!adj_window_config(g, p, src, c)) return RS_ERR_UNSUPPORTED;
-    c.aa_method = method;
-    c.aa_a = o.cubic_a;
+    c.tap_method = method;
+    c.tap_a = o.cubic_a;
     return cuda_status(launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst), AdjTables{},
-                                         c, st, true));
+                                         c, st, TAPS_AA));
+}
+
+// Host ranges of the point taps in the window pass's forward roles: rows
+// keep the unclamped first tap (the staging clamps rows), columns start at
+// max(first tap, 0) (the kernel merges clamped taps), as in k_adj_window.
+static AxisRanges point_ranges(int n, int m, int method, int coord, bool columns)
+{
+    const int K = method_taps(method);
+    AxisRanges R;
+    R.lo.resize(m);
+    R.hi.resize(m);
+    for (int j = 0; j < m; ++j) {
+        const int f = host_first_tap(j, n, m, method, coord);
+        R.lo[j] = columns ? std::max(f, 0) : f;
+        R.hi[j] = R.lo[j] + K - 1;
+    }
+    R.kmax = K;
+    return R;
+}
+
+// The forward resampling through the fused window pass in its transposed
+// roles (RS_IMPL_REDUCE): FP32 bilinear / bicubic, source rows of whole
+// 16-byte units. Returns false where it does not apply.
+static bool reduce_setup(const Geom& gf, int method, int dtype, const void* src, Geom& g, BwdPlan& p, AdjWinCfg& c)
+{
+    if (dtype != DT_F32 || (method != M_BILINEAR && method != M_BICUBIC)) return false;
+    g = gf;
+    g.H = gf.Ho; g.W = gf.Wo; g.Ho = gf.H; g.Wo = gf.W;
+    g.sp = gf.dp; g.dp = gf.sp;
+    g.src_pitch = gf.dst_pitch; g.dst_pitch = gf.src_pitch;
+    p.ry = point_ranges(gf.H, gf.Ho, method, gf.coord, false);
+    p.rx = point_ranges(gf.W, gf.Wo, method, gf.coord, true);
+    p.yK = p.xK = method_taps(method);
+    if (!adj_window_config(g, p, src, c)) return false;
+    c.tap_method = method;
+    c.tap_a = gf.a;
+    return true;
+}
+
+bool reduce_config(const Geom& gf, int method, int dtype, const void* src, size_t* smem)
+{
+    Geom g;
+    BwdPlan p;
+    AdjWinCfg c;
+    if (!reduce_setup(gf, method, dtype, src, g, p, c)) return false;
+    if (smem) *smem = c.smem;
+    return true;
+}
+
+cudaError_t launch_reduce(const Geom& gf, int method, int dtype, const void* src, void* dst, cudaStream_t st)
+{
+    Geom g;
+    BwdPlan p;
+    AdjWinCfg c;
+    if (!reduce_setup(gf, method, dtype, src, g, p, c)) return cudaErrorInvalidValue;
+    return launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst), AdjTables{}, c, st,
+                             TAPS_POINT);
 }
 
 template <int KX, int C>

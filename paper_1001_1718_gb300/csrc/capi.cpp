@@ -30,7 +30,7 @@ rs_status check_options(const rs_options& o, int method)
 {
     if (o.coord != RS_COORD_ASYMMETRIC && o.coord != RS_COORD_HALF_PIXEL) return RS_ERR_INVALID_ARG;
     if (!std::isfinite(o.cubic_a)) return RS_ERR_INVALID_ARG;
-    if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_WINDOW) return RS_ERR_INVALID_ARG;
+    if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_REDUCE) return RS_ERR_INVALID_ARG;
     if (o.tile_w < 0 || o.tile_h < 0 || o.threads < 0 || o.waves < 0) return RS_ERR_INVALID_ARG;
     if (o.flags & ~RS_FLAG_ANTIALIAS) return RS_ERR_INVALID_ARG;
     if (method < RS_NEAREST || method > RS_BICUBIC) return RS_ERR_INVALID_ARG;

@@ -27,7 +27,7 @@ rs_status make_geom(const void* src, const rs_layout* in, const void* dst, const
 // Kernel and configuration for a forward call: explicit options, else the
 // tuning cache, else the default (streaming kernel when it fits).
 struct KernelChoice {
-    int impl;        // RS_IMPL_STREAM, RS_IMPL_TILED or RS_IMPL_GATHER
+    int impl;        // RS_IMPL_STREAM, RS_IMPL_TILED, RS_IMPL_GATHER, RS_IMPL_WINDOW or RS_IMPL_REDUCE
     TileCfg tile;
     StreamCfg stream;
     int gather_w, gather_rows;   // RS_IMPL_GATHER: strip width, rows per thread
@@ -44,6 +44,11 @@ cudaError_t read_fault(cudaStream_t st, unsigned int* code);
 // computed taps).
 rs_status resize_antialias(const Geom& g, int method, int dtype, const void* src, void* dst, const rs_options& o,
                            cudaStream_t st);
+// RS_IMPL_REDUCE forward (backward.cu: the fused window pass with the
+// point taps of Eqs. 1-5 computed in the kernel). reduce_config: whether it
+// applies, and its dynamic shared memory.
+bool reduce_config(const Geom& g, int method, int dtype, const void* src, size_t* smem);
+cudaError_t launch_reduce(const Geom& g, int method, int dtype, const void* src, void* dst, cudaStream_t st);
 
 // Tuning cache entry: kernel (rs_impl) and shape; see autotune.cpp.
 struct Tuned {

@@ -170,6 +170,18 @@ def test_tile_config_query_without_buffers(L):
     assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_U8, B.RS_BICUBIC, None,
                                 ctypes.byref(c)) == 0
     assert c.impl == B.RS_IMPL_WINDOW and c.tile_w == 1024 and c.tile_h in (4, 8)
+    # an FP32 x0.5 downscale runs the window pass in its transposed roles;
+    # uint8 does not (it stores bytes; REDUCE is FP32 only)
+    Li, Lo = L.rs_layout_nchw(32, 3, 512, 512), L.rs_layout_nchw(32, 3, 256, 256)
+    for m in (B.RS_BILINEAR, B.RS_BICUBIC):
+        assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, m, None, ctypes.byref(c)) == 0
+        assert c.impl == B.RS_IMPL_REDUCE
+    assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_U8, B.RS_BICUBIC, None, ctypes.byref(c)) == 0
+    assert c.impl != B.RS_IMPL_REDUCE
+    # an explicit REDUCE takes no shape parameters
+    o = B.options(impl=B.RS_IMPL_REDUCE, tile_w=512)
+    assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, B.RS_BILINEAR, ctypes.byref(o),
+                                ctypes.byref(c)) != 0
     del rs
 
 

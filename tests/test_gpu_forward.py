@@ -306,6 +306,64 @@ def test_window_shifted_staging(rs, oracle, dtype):
     assert rs.debug_fault() == 0
 
 
+REDUCE_CASES = [
+    # (N, C, H, W, Ho, Wo, coord); NCHW, W a multiple of 4
+    (2, 3, 64, 80, 32, 40, 0),         # x0.5
+    (1, 2, 100, 124, 37, 51, 1),       # ragged downscale, half-pixel
+    (1, 1, 700, 1200, 300, 600, 0),    # two strips, bands of 256 rows and a tail
+    (1, 1, 33, 20, 9, 5, 1),           # near 1/4: edge taps clamp on both sides
+    (2, 4, 40, 36, 90, 72, 1),         # an upscale (any scale applies)
+    (1, 1, 4, 4, 1, 1, 0),             # one output pixel
+    (1, 3, 512, 512, 256, 256, 1),     # the NCHW x0.5 workload's plane shape
+]
+
+
+@pytest.mark.parametrize("method", [BL, BC])
+def test_reduce_matches_oracle(rs, oracle, method):
+    """RS_IMPL_REDUCE (the fused window pass in its transposed roles, point
+    taps of Eqs. 1-5 computed in the kernel, clamped edge taps merged)
+    against the FP64 oracle: NCHW and interleaved, both coordinate maps,
+    ragged strips and bands."""
+    for k, (N, C, H, W, Ho, Wo, coord) in enumerate(REDUCE_CASES):
+        t, x64 = _src(1600 + k, (N, C, H, W), "f32")
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="reduce")
+        torch.cuda.synchronize()
+        check(y, oracle.resize_nchw(x64, Ho, Wo, method, coord), "f32", method, np.abs(x64).max(),
+              f"reduce nchw {MNAME[method]} {CNAME[coord]} {(N, C, H, W)}->{Ho}x{Wo}")
+    for k, (H, W, C, Ho, Wo) in enumerate([(90, 128, 3, 45, 50), (256, 200, 3, 64, 52), (61, 77, 4, 30, 20)]):
+        t, x64 = _src(1700 + k, (H, W, C), "f32")
+        for coord in (0, 1):
+            y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], coord=CNAME[coord], impl="reduce")
+            torch.cuda.synchronize()
+            check(y, oracle.resize(x64, Ho, Wo, method, coord), "f32", method, np.abs(x64).max(),
+                  f"reduce hwc {MNAME[method]} {CNAME[coord]} {H}x{W}x{C}->{Ho}x{Wo}")
+    if method == BC:   # another Keys parameter
+        t, x64 = _src(1800, (1, 2, 96, 64), "f32")
+        y = rs.resize(t.cuda(), (40, 30), "bicubic", layout="nchw", cubic_a=-0.75, impl="reduce")
+        torch.cuda.synchronize()
+        check(y, oracle.resize_nchw(x64, 40, 30, BC, 0, a=-0.75), "f32", BC, np.abs(x64).max(), "reduce a=-0.75")
+    assert rs.debug_fault() == 0
+
+
+def test_reduce_auto_and_refusals(rs, oracle):
+    """AUTO takes REDUCE for a large FP32 vertical downscale, and the result
+    matches the oracle; REDUCE refuses what it does not cover."""
+    x = torch.randn(8, 3, 512, 512, device="cuda")
+    assert rs.tile_config(x, (256, 256), "bilinear", layout="nchw")["impl"] == "reduce"
+    y = rs.resize(x, (256, 256), "bicubic", layout="nchw")
+    ref = oracle.resize_nchw(x[1:2].double().cpu().numpy(), 256, 256, BC, 0)
+    check(y[1:2], ref, "f32", BC, float(x.abs().max()), "auto reduce x0.5")
+    with pytest.raises(rs.ResampleError):          # FP32 only
+        rs.resize(torch.zeros(64, 64, dtype=torch.uint8, device="cuda"), (32, 32), "bilinear", impl="reduce")
+    with pytest.raises(rs.ResampleError):          # nearest has its own gather
+        rs.resize(torch.zeros(64, 64, device="cuda"), (32, 32), "nearest", impl="reduce")
+    with pytest.raises(rs.ResampleError):          # rows of 63 FP32 elements are not whole 16-byte units
+        rs.resize(torch.zeros(64, 63, device="cuda"), (32, 32), "bilinear", impl="reduce")
+    with pytest.raises(rs.ResampleError):          # no shape parameters
+        rs.resize(torch.zeros(64, 64, device="cuda"), (32, 32), "bilinear", impl="reduce", tile=(512, 4))
+    assert rs.debug_fault() == 0
+
+
 @pytest.mark.parametrize("method", [BL, BC])
 def test_antialias_matches_oracle(rs, oracle, method):
     """RS_FLAG_ANTIALIAS (the kernel stretched by the downscale factor, taps
