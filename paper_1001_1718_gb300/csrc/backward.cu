@@ -357,9 +357,9 @@ k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const
 // ---------------------------------------------------------------------------
 // Fused register-window adjoint (FP32, dY rows of whole 16-byte units).
 //
-// The transpose of the forward's register window. A block owns a strip of
-// 2 x 256 dX elements and a band of dX rows; thread t owns elements t and
-// t + 256. It walks the rows of T = dY Ax that the band's y taps reach
+// The transpose of the forward's register window. A block of NT threads
+// owns a strip of 2 NT dX elements and a band of dX rows; thread t owns
+// elements t and t + NT. It walks the rows of T = dY Ax that the band's y taps reach
 // ("positions"): each dY row, staged in shared memory, is x-adjointed at
 // the thread's two columns into a register window of the last KY such
 // rows, and every dX row whose first y tap is the window's first row is
@@ -369,6 +369,7 @@ k_adj_y(const Geom g, const float* __restrict__ T, float* __restrict__ dX, const
 // each ascending), so the results equal the two-pass kernels'.
 struct AdjWinCfg {
     int band_h, band_cap, pos_cap, chunk, swe_max;
+    int nt;          // threads per block (strips of 2 nt dX elements)
     int tap_method;  // computed taps (TAPS_AA, TAPS_POINT): M_BILINEAR / M_BICUBIC
     float tap_a;     // Keys parameter of the bicubic kernel
     size_t smem;
@@ -430,8 +431,9 @@ __device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a
     #pragma unroll
     for (int k = 0; k < K; ++k) w[k] *= inv;
 }
+// Threads per block: 256 (strips of 512 dX elements), or 128 (strips of
+// 256) for the computed-tap modes where that pads narrow rows less.
 static constexpr int kAwThreads = 256;
-static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
 
 // Where the taps come from. TAPS_TABLE: the transposed tables of the
 // adjoint. TAPS_AA / TAPS_POINT: the same pass as a forward resampling, the
@@ -443,8 +445,8 @@ static constexpr int kAwElems = 2 * kAwThreads;   // dX elements per strip
 // consecutive staged columns from max(first tap, 0).
 enum { TAPS_TABLE = 0, TAPS_AA = 1, TAPS_POINT = 2 };
 
-template <int C, int KX, int KY, int TM>
-__global__ void __launch_bounds__(kAwThreads, 2)
+template <int C, int KX, int KY, int TM, int NT = kAwThreads>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX, const AdjTables tb,
              const AdjWinCfg cfg, unsigned int* fault)
 {
@@ -454,8 +456,8 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     const float* s = dY + g.dp.offset(plane);   // Ho rows of Wo C, pitch dst_pitch
     float* d = dX + g.sp.offset(plane);         // H rows of W C, pitch src_pitch
     const int WC = g.W * C, WoC = g.Wo * C;
-    const int e0 = blockIdx.x * kAwElems;
-    const int nE = min(kAwElems, WC - e0);
+    const int e0 = blockIdx.x * (2 * NT);
+    const int nE = min((2 * NT), WC - e0);
     const int yb = blockIdx.y * cfg.band_h;
     const int nrows = min(cfg.band_h, g.H - yb);
 
@@ -488,12 +490,12 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     int* NC = RF + cfg.band_cap;                                 // [pos_cap] rows per position
     if (c_hi > WoC) {
         const int z0 = WoC - a0, zn = c_hi - WoC;
-        for (int u = tid; u < 3 * R * zn; u += kAwThreads) {
+        for (int u = tid; u < 3 * R * zn; u += NT) {
             const int row = u / zn;
             RING[row * cfg.swe_max + z0 + (u - row * zn)] = 0.0f;
         }
     }
-    for (int i = tid; i < nrows; i += kAwThreads) {
+    for (int i = tid; i < nrows; i += NT) {
         const int r = yb + i;
         if constexpr (TM == TAPS_AA) {
             float w[KY];
@@ -519,7 +521,7 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
         float wx[2][KX];
         #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int el = tid + kAwThreads * k;
+            const int el = tid + NT * k;
             if (el < nE) {
                 const int e = e0 + el, x = e / C, c = e - x * C;
                 int lo;
@@ -553,14 +555,14 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
         #pragma unroll
         for (int q = 0; q < KX; ++q) wxp[q] = make_float2(wx[0][q], wx[1][q]);
     }
-    for (int p = tid; p < cfg.pos_cap; p += kAwThreads) NC[p] = 0;
+    for (int p = tid; p < cfg.pos_cap; p += NT) NC[p] = 0;
     __syncthreads();
     const int b_first = RF[0], b_last = RF[nrows - 1];
     if (b_last - b_first + 1 > cfg.pos_cap) {   // uniform; the host bounds the positions
         if (tid == 0) report_fault(fault, FAULT_BWD_SPAN);
         return;
     }
-    for (int i0 = tid; i0 < nrows; i0 += kAwThreads) {
+    for (int i0 = tid; i0 < nrows; i0 += NT) {
         if (i0 == 0 || RF[i0] != RF[i0 - 1]) {
             int len = 1;
             while (i0 + len < nrows && RF[i0 + len] == RF[i0]) ++len;
@@ -575,7 +577,7 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     auto issue = [&](int c) {
         const int r0 = r_first + c * R, nn = chunk_rows(c);
         float* slot = RING + (c % 3) * R * cfg.swe_max;
-        for (int u = tid; u < nn * units; u += kAwThreads) {
+        for (int u = tid; u < nn * units; u += NT) {
             const int k = units > 1 ? (int)__umulhi((uint32_t)u, umul) : u;
             const int w = u - k * units;
             const float* src = s + (int64_t)clampi(r0 + k, g.Ho) * g.dst_pitch + a0 + 4 * w;
@@ -601,7 +603,7 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     int r = b_first + KY - 1, cidx = 0, chunk_lo = r_first;
     int nn = chunk_rows(0);
     int i = 0, b = b_first;
-    const int nact = (tid < nE) + (tid + kAwThreads < nE);
+    const int nact = (tid < nE) + (tid + NT < nE);
     float* const dband = d + (int64_t)yb * g.src_pitch + e0 + tid;
     const int pitch32 = (int)g.src_pitch;
     auto blend_put = [&](int row, const int* slot) {
@@ -613,7 +615,7 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
         }
         float* q = dband + row * pitch32;
         if (nact > 0) q[0] = v.x;
-        if (nact > 1) q[kAwThreads] = v.y;
+        if (nact > 1) q[NT] = v.y;
     };
     while (b <= b_last) {
         #pragma unroll
@@ -714,7 +716,7 @@ static int adj_taps_class(int k) { return k <= 2 ? 2 : k <= 4 ? 4 : 8; }
 
 // The fused window adjoint applies with at most 8 transposed taps per axis,
 // dY rows of whole 16-byte units and a footprint that fits shared memory.
-static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, AdjWinCfg& c)
+static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, AdjWinCfg& c, bool narrow = false)
 {
     if (p.xK > 8 || p.yK > 8) return false;
     const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
@@ -722,9 +724,12 @@ static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, A
     if (g.planes > 1 && (g.dp.n_stride % 4 || g.dp.c_stride % 4)) return false;
     c.chunk = std::max(4, KY);
     const int WC = g.W * g.C;
+    // 128-thread blocks where strips of 256 pad the rows less than strips of 512
+    c.nt = narrow && (WC + 255) / 256 * 256 < (WC + 511) / 512 * 512 ? 128 : kAwThreads;
+    const int elems = 2 * c.nt;
     int swe = 4;
-    for (int e0 = 0; e0 < WC; e0 += kAwElems) {
-        const int nE = std::min(kAwElems, WC - e0);
+    for (int e0 = 0; e0 < WC; e0 += elems) {
+        const int nE = std::min(elems, WC - e0);
         const int xf = e0 / g.C, xl = (e0 + nE - 1) / g.C;
         const int a0 = (p.rx.lo[xf] * g.C) & ~3;
         swe = std::max(swe, (p.rx.lo[xl] + KX) * g.C - a0);
@@ -745,26 +750,33 @@ static bool adj_window_config(const Geom& g, const BwdPlan& p, const void* dY, A
 }
 
 template <int C, int KX, int KY>
-static void* adj_window_func(int tm)
+static void* adj_window_func(int tm, int nt)
 {
-    return tm == TAPS_AA ? reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_AA>)
-                         : reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_TABLE>);
+    if (tm == TAPS_AA)
+        return nt == 128 ? reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_AA, 128>)
+                         : reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_AA>);
+    return reinterpret_cast<void*>(&k_adj_window<C, KX, KY, TAPS_TABLE>);
 }
 
 template <int C, int KX>
-static void* adj_window_fy(int KY, int tm)
+static void* adj_window_fy(int KY, int tm, int nt)
 {
-    return KY == 2 ? adj_window_func<C, KX, 2>(tm) : KY == 4 ? adj_window_func<C, KX, 4>(tm)
-                                                           : adj_window_func<C, KX, 8>(tm);
+    return KY == 2 ? adj_window_func<C, KX, 2>(tm, nt) : KY == 4 ? adj_window_func<C, KX, 4>(tm, nt)
+                                                               : adj_window_func<C, KX, 8>(tm, nt);
 }
 
 template <int C>
-static void* adj_window_fx(int KX, int KY, int tm)
+static void* adj_window_fx(int KX, int KY, int tm, int nt)
 {
-    if (tm == TAPS_POINT)   // the method's own taps on both axes: KX == KY in {2, 4}
+    if (tm == TAPS_POINT) {   // the method's own taps on both axes: KX == KY in {2, 4}
+        if (nt == 128)
+            return KX == 2 ? reinterpret_cast<void*>(&k_adj_window<C, 2, 2, TAPS_POINT, 128>)
+                           : reinterpret_cast<void*>(&k_adj_window<C, 4, 4, TAPS_POINT, 128>);
         return KX == 2 ? reinterpret_cast<void*>(&k_adj_window<C, 2, 2, TAPS_POINT>)
                        : reinterpret_cast<void*>(&k_adj_window<C, 4, 4, TAPS_POINT>);
-    return KX == 2 ? adj_window_fy<C, 2>(KY, tm) : KX == 4 ? adj_window_fy<C, 4>(KY, tm) : adj_window_fy<C, 8>(KY, tm);
+    }
+    return KX == 2 ? adj_window_fy<C, 2>(KY, tm, nt) : KX == 4 ? adj_window_fy<C, 4>(KY, tm, nt)
+                                                               : adj_window_fy<C, 8>(KY, tm, nt);
 }
 
 static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const float* dY, float* dX, const AdjTables& tb,
@@ -772,21 +784,22 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
 {
     const int KX = adj_taps_class(p.xK), KY = adj_taps_class(p.yK);
     if (tm == TAPS_POINT && (KX != KY || KX > 4)) return cudaErrorInvalidValue;
-    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, tm) : g.C == 2 ? adj_window_fx<2>(KX, KY, tm)
-               : g.C == 3 ? adj_window_fx<3>(KX, KY, tm) : adj_window_fx<4>(KX, KY, tm);
+    if (c.nt != kAwThreads && (c.nt != 128 || tm == TAPS_TABLE)) return cudaErrorInvalidValue;
+    void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, tm, c.nt) : g.C == 2 ? adj_window_fx<2>(KX, KY, tm, c.nt)
+               : g.C == 3 ? adj_window_fx<3>(KX, KY, tm, c.nt) : adj_window_fx<4>(KX, KY, tm, c.nt);
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kAwThreads, c.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, c.nt, c.smem);
     if (e != cudaSuccess) return e;
-    const int64_t strips = ((int64_t)g.W * g.C + kAwElems - 1) / kAwElems;
+    const int64_t strips = ((int64_t)g.W * g.C + 2 * c.nt - 1) / (2 * c.nt);
     const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
     const int64_t bands = std::max<int64_t>(1, (2 * resident + strips * g.planes - 1) / (strips * g.planes));
     c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.H + bands - 1) / bands));
     dim3 grid((unsigned)strips, (unsigned)((g.H + c.band_h - 1) / c.band_h), (unsigned)g.planes);
     unsigned int* fw = fault_word();
     void* args[] = {const_cast<Geom*>(&g), const_cast<float**>(&dY), &dX, const_cast<AdjTables*>(&tb), &c, &fw};
-    e = cudaLaunchKernel(func, grid, dim3(kAwThreads), args, c.smem, st);
+    e = cudaLaunchKernel(func, grid, dim3(c.nt), args, c.smem, st);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -824,7 +837,7 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
     p.yK = std::max(1, p.ry.kmax);
     p.xK = std::max(1, p.rx.kmax);
     AdjWinCfg c;
-    if (!adj_window_config(g, p, src, c)) return RS_ERR_UNSUPPORTED;
+    if (!adj_window_config(g, p, src, c, true)) return RS_ERR_UNSUPPORTED;
     c.tap_method = method;
     c.tap_a = o.cubic_a;
     return cuda_status(launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst), AdjTables{},
@@ -862,7 +875,7 @@ static bool reduce_setup(const Geom& gf, int method, int dtype, const void* src,
     p.ry = point_ranges(gf.H, gf.Ho, method, gf.coord, false);
     p.rx = point_ranges(gf.W, gf.Wo, method, gf.coord, true);
     p.yK = p.xK = method_taps(method);
-    if (!adj_window_config(g, p, src, c)) return false;
+    if (!adj_window_config(g, p, src, c, true)) return false;
     c.tap_method = method;
     c.tap_a = gf.a;
     return true;
