@@ -23,7 +23,7 @@ BUILD = HERE / "_build"
 LIB = BUILD / "liboracle.so"
 
 NEAREST, BILINEAR, BICUBIC = 0, 1, 2
-ASYMMETRIC, HALF_PIXEL = 0, 1
+ASYMMETRIC, HALF_PIXEL, ALIGN_CORNERS = 0, 1, 2
 
 _lib = None
 

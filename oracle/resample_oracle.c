@@ -12,9 +12,13 @@
  *   1. Map (Eq. 1). The paper's x_p = x_f / scale with scale = m / n taken
  *      from the sizes, so x = j * n / m, held as the exact rational
  *      num / den (ASYMMETRIC). The half-pixel option maps pixel centres:
- *      x = (j + 1/2) * n / m - 1/2 = ((2j + 1) n - m) / (2 m).
+ *      x = (j + 1/2) * n / m - 1/2 = ((2j + 1) n - m) / (2 m). The
+ *      align-corners option (an extension; the paper has one map) pins
+ *      the first and last samples of both axes together:
+ *      x = j (n - 1) / (m - 1), and x = 0 when m = 1.
  *   2. Base and fraction (Eqs. 2-4): i0 = floor(x), t = x - i0.
- *   3. Taps. nearest: i0 (ASYMMETRIC) or floor(x + 1/2) (HALF_PIXEL), weight
+ *   3. Taps. nearest: i0 (ASYMMETRIC) or floor(x + 1/2) (HALF_PIXEL and
+ *      ALIGN_CORNERS), weight
  *      1. bilinear: i0, i0+1 with weights 1-t, t (Eq. 5 with its second
  *      (1 - offsetY) read as (1 - offsetX)). bicubic: i0-1 .. i0+2 with
  *      weights K(t+1), K(t), K(1-t), K(2-t) for Keys' cubic convolution
@@ -46,7 +50,7 @@
 #endif
 
 enum { M_NEAREST = 0, M_BILINEAR = 1, M_BICUBIC = 2 };
-enum { C_ASYMMETRIC = 0, C_HALF_PIXEL = 1 };
+enum { C_ASYMMETRIC = 0, C_HALF_PIXEL = 1, C_ALIGN_CORNERS = 2 };
 
 /* floor(num / den) for den > 0 and any sign of num. */
 static int64_t floor_div(int64_t num, int64_t den)
@@ -83,9 +87,15 @@ static int axis_taps(int64_t j, int64_t n, int64_t m, int method, int coord,
     if (coord == C_ASYMMETRIC) {          /* x = j n / m */
         num = j * n;
         den = m;
-    } else {                              /* x = ((2j+1) n - m) / (2m) */
+    } else if (coord == C_HALF_PIXEL) {   /* x = ((2j+1) n - m) / (2m) */
         num = (2 * j + 1) * n - m;
         den = 2 * m;
+    } else if (m > 1) {                   /* x = j (n-1) / (m-1) */
+        num = j * (n - 1);
+        den = m - 1;
+    } else {                              /* one output sample: x = 0 */
+        num = 0;
+        den = 1;
     }
     int64_t i0 = floor_div(num, den);
     double t = (double)(num - i0 * den) / (double)den;
@@ -95,6 +105,9 @@ static int axis_taps(int64_t j, int64_t n, int64_t m, int method, int coord,
         if (coord == C_HALF_PIXEL) {
             /* floor(x + 1/2) = floor((2j+1) n / (2m)) */
             i = floor_div((2 * j + 1) * n, 2 * m);
+        } else if (coord == C_ALIGN_CORNERS) {
+            /* floor(x + 1/2) = floor((2 num + den) / (2 den)) */
+            i = floor_div(2 * num + den, 2 * den);
         }
         idx[0] = clampi(i, n);
         w[0] = 1.0;

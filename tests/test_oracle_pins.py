@@ -15,9 +15,9 @@ import pytest
 
 GOLDEN = Path(__file__).resolve().parent / "golden"
 NN, BL, BC = 0, 1, 2
-ASYM, HALF = 0, 1
+ASYM, HALF, ALIGN = 0, 1, 2
 METHODS = (NN, BL, BC)
-COORDS = (ASYM, HALF)
+COORDS = (ASYM, HALF, ALIGN)
 
 
 def _rng(seed):
@@ -25,10 +25,13 @@ def _rng(seed):
 
 
 def _coord(j, n, m, coord):
-    """Source coordinate of output index j (Eq. 1; half-pixel variant)."""
+    """Source coordinate of output index j (Eq. 1; half-pixel and
+    align-corners variants)."""
     j = np.asarray(j, np.float64)
     if coord == ASYM:
         return j * n / m
+    if coord == ALIGN:
+        return j * (n - 1) / (m - 1) if m > 1 else 0.0 * j
     return (j + 0.5) * n / m - 0.5
 
 
@@ -232,6 +235,43 @@ def test_half_pixel_matches_torch(oracle, shape):
     tc = F.interpolate(tx, size=(Ho, Wo), mode="bicubic", align_corners=False).numpy()
     assert np.abs(oracle.resize_nchw(x, Ho, Wo, BL, HALF) - tb).max() < 1e-12
     assert np.abs(oracle.resize_nchw(x, Ho, Wo, BC, HALF, -0.75) - tc).max() < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(7, 9, 13, 20), (9, 7, 4, 5), (16, 12, 8, 6), (5, 40, 11, 17), (6, 5, 1, 9)])
+def test_align_corners_matches_torch(oracle, shape):
+    """torch bilinear / bicubic with align_corners=True use the map
+    x = j (n - 1) / (m - 1) (x = 0 for one output), edge clamping and (for
+    bicubic) Keys' kernel with a = -3/4."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    H, W, Ho, Wo = shape
+    x = _rng(17).standard_normal((2, 3, H, W))
+    tx = torch.from_numpy(x)
+    tb = F.interpolate(tx, size=(Ho, Wo), mode="bilinear", align_corners=True).numpy()
+    tc = F.interpolate(tx, size=(Ho, Wo), mode="bicubic", align_corners=True).numpy()
+    assert np.abs(oracle.resize_nchw(x, Ho, Wo, BL, ALIGN) - tb).max() < 1e-12
+    assert np.abs(oracle.resize_nchw(x, Ho, Wo, BC, ALIGN, -0.75) - tc).max() < 1e-12
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_align_corners_keeps_corners(oracle, method):
+    """Under align-corners the four corner samples land exactly on the four
+    corner outputs, at any scale, for every method."""
+    x = _rng(18).standard_normal((11, 14, 2))
+    for Ho, Wo in ((23, 5), (4, 31), (11, 14), (2, 2)):
+        y = oracle.resize(x, Ho, Wo, method, ALIGN)
+        for (a, b), (c, d) in (((0, 0), (0, 0)), ((0, -1), (0, -1)), ((-1, 0), (-1, 0)), ((-1, -1), (-1, -1))):
+            assert np.array_equal(y[a, b], x[c, d])
+
+
+def test_align_corners_nearest_rounds(oracle):
+    """Align-corners nearest takes the sample nearest to j (n - 1) / (m - 1)
+    (ties upward), by exact rational arithmetic."""
+    for n, m in ((7, 16), (16, 7), (10, 17), (31, 9), (5, 5), (9, 1), (2, 40)):
+        idx, _ = oracle.axis_taps(n, m, NN, ALIGN)
+        for j in range(m):
+            x = Fraction(j * (n - 1), m - 1) if m > 1 else Fraction(0)
+            assert idx[j, 0] == int(np.floor(x + Fraction(1, 2)))
 
 
 @pytest.mark.parametrize("method", METHODS)
