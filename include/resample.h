@@ -13,8 +13,11 @@
  *   - scale is m / n, taken from the sizes, so x = j * n / m exactly
  *     (RS_COORD_ASYMMETRIC, the paper's Eq. 1); RS_COORD_HALF_PIXEL maps
  *     pixel centres instead: x = (j + 1/2) * n / m - 1/2;
+ *     RS_COORD_ALIGN_CORNERS (an extension) pins the first and last
+ *     samples together: x = j * (n - 1) / (m - 1), x = 0 when m = 1;
  *   - i0 = floor(x), t = x - i0 (Eqs. 2-4);
- *   - RS_NEAREST: sample i0 (asymmetric) or floor(x + 1/2) (half-pixel);
+ *   - RS_NEAREST: sample i0 (asymmetric) or floor(x + 1/2) (half-pixel,
+ *     align-corners);
  *     RS_BILINEAR: samples i0, i0+1, weights 1-t, t (Eq. 5);
  *     RS_BICUBIC: samples i0-1 .. i0+2, weights K(t+1), K(t), K(1-t), K(2-t)
  *     with Keys' cubic convolution kernel K of parameter a (default -1/2);
@@ -58,7 +61,7 @@ typedef enum {
 
 typedef enum { RS_U8 = 0, RS_F16 = 1, RS_BF16 = 2, RS_F32 = 3 } rs_dtype;
 typedef enum { RS_NEAREST = 0, RS_BILINEAR = 1, RS_BICUBIC = 2 } rs_method;
-typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1 } rs_coord;
+typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1, RS_COORD_ALIGN_CORNERS = 2 } rs_coord;
 
 /* Kernel selection.
  * AUTO   = the tuned (or default) kernel for the problem: GATHER for

@@ -21,7 +21,8 @@ from . import _binding as B
 from ._binding import ResampleError, lib
 
 METHODS = {"nearest": B.RS_NEAREST, "bilinear": B.RS_BILINEAR, "bicubic": B.RS_BICUBIC}
-COORDS = {"asymmetric": B.RS_COORD_ASYMMETRIC, "half_pixel": B.RS_COORD_HALF_PIXEL}
+COORDS = {"asymmetric": B.RS_COORD_ASYMMETRIC, "half_pixel": B.RS_COORD_HALF_PIXEL,
+          "align_corners": B.RS_COORD_ALIGN_CORNERS}
 IMPLS = {"auto": B.RS_IMPL_AUTO, "tiled": B.RS_IMPL_TILED, "plain": B.RS_IMPL_PLAIN,
          "stream": B.RS_IMPL_STREAM, "gather": B.RS_IMPL_GATHER, "window": B.RS_IMPL_WINDOW,
          "reduce": B.RS_IMPL_REDUCE}

@@ -14,7 +14,7 @@ LIB_PATH = PKG / "_lib" / "libresample.so"
 RS_OK, RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED, RS_ERR_ALIGNMENT, RS_ERR_WORKSPACE, RS_ERR_CUDA = range(6)
 RS_U8, RS_F16, RS_BF16, RS_F32 = range(4)
 RS_NEAREST, RS_BILINEAR, RS_BICUBIC = range(3)
-RS_COORD_ASYMMETRIC, RS_COORD_HALF_PIXEL = range(2)
+RS_COORD_ASYMMETRIC, RS_COORD_HALF_PIXEL, RS_COORD_ALIGN_CORNERS = range(3)
 RS_IMPL_AUTO, RS_IMPL_TILED, RS_IMPL_PLAIN, RS_IMPL_STREAM, RS_IMPL_GATHER, RS_IMPL_WINDOW, RS_IMPL_REDUCE = range(7)
 RS_FLAG_ANTIALIAS = 1
 RS_NOALLOC_MAX_IMAGES = 4096

@@ -39,6 +39,12 @@ static int64_t host_floor_div(int64_t num, int64_t den)
 
 static int host_first_tap(int j, int n, int m, int method, int coord)
 {
+    if (coord == COORD_ALIGN_CORNERS) {   // x = j (n - 1) / (m - 1); 0 for one output
+        const int64_t num = m > 1 ? (int64_t)j * (n - 1) : 0, den = m > 1 ? m - 1 : 1;
+        if (method == M_NEAREST) return (int)host_floor_div(2 * num + den, 2 * den);
+        const int64_t i0 = host_floor_div(num, den);
+        return (int)(method == M_BICUBIC ? i0 - 1 : i0);
+    }
     if (method == M_NEAREST) {
         if (coord == COORD_ASYMMETRIC) return (int)host_floor_div((int64_t)j * n, m);
         return (int)host_floor_div((int64_t)(2 * j + 1) * n, 2 * (int64_t)m);

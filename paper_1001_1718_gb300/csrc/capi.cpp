@@ -28,7 +28,7 @@ rs_options options_or_default(const rs_options* opt)
 
 rs_status check_options(const rs_options& o, int method)
 {
-    if (o.coord != RS_COORD_ASYMMETRIC && o.coord != RS_COORD_HALF_PIXEL) return RS_ERR_INVALID_ARG;
+    if (o.coord < RS_COORD_ASYMMETRIC || o.coord > RS_COORD_ALIGN_CORNERS) return RS_ERR_INVALID_ARG;
     if (!std::isfinite(o.cubic_a)) return RS_ERR_INVALID_ARG;
     if (o.impl < RS_IMPL_AUTO || o.impl > RS_IMPL_REDUCE) return RS_ERR_INVALID_ARG;
     if (o.tile_w < 0 || o.tile_h < 0 || o.threads < 0 || o.waves < 0) return RS_ERR_INVALID_ARG;

@@ -377,13 +377,15 @@ static bool nn_rows_ok(const Geom& g, int dtype, const void* src, const void* ds
 }
 
 // Upper bound of the 16-byte units a strip of 4096 output bytes reads from
-// one source row: its source bytes span at most (4096 / C / es / scale + 1)
-// pixels.
+// one source row: its source bytes span at most (4096 / C / es) times the
+// coordinate's advance per output, plus one, pixels.
 static int nn_rows_units(const Geom& g, int dtype)
 {
     const int64_t es = (int64_t)dtype_size(dtype);
     const int64_t px_out = kNnStripBytes / (g.C * es) + 2;
-    const int64_t px_src = (px_out * g.W + g.Wo - 1) / g.Wo + 2;
+    int64_t an, am;
+    coord_advance(g.W, g.Wo, g.coord, an, am);
+    const int64_t px_src = (px_out * an + am - 1) / am + 2;
     return (int)((px_src * g.C * es + 15) / 16 + 2);
 }
 

@@ -31,12 +31,6 @@ k_poly(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const PolyC
 // Host side
 
 #if POLY_MODE == 1
-static int poly_span_bound(int k, int n, int m, int KT)
-{
-    const int64_t num = (int64_t)(k - 1) * n;
-    return (int)((num + m - 1) / m) + KT;
-}
-
 bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c, bool shifted_only)
 {
     if (method != M_BILINEAR && method != M_BICUBIC) return false;
@@ -50,11 +44,11 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
             (!planar || ((g.sp.n_stride * es) % 16 == 0 && (g.sp.c_stride * es) % 16 == 0)) && !shifted_only ? 1 : 2;
     const int EPU = c.vec ? 16 / es : 1;
     const int kpx = (kPolyElems + g.C - 1) / g.C + 1;
-    const int span_px = poly_span_bound(kpx, g.W, g.Wo, KT);
+    const int span_px = tap_span_bound(kpx, g.W, g.Wo, KT, g.coord);
     c.swe_max = ((span_px * g.C + 2 * EPU + 4) + 3) & ~3;
     c.band_cap = std::min(kPolyMaxBand, g.Ho);
     if ((int64_t)c.band_cap * g.dst_pitch >= (int64_t)INT32_MAX) return false;   // 32-bit row offsets
-    c.pos_cap = poly_span_bound(c.band_cap, g.H, g.Ho, KT);   // source positions of a band
+    c.pos_cap = tap_span_bound(c.band_cap, g.H, g.Ho, KT, g.coord);   // source positions of a band
     const size_t tables = sizeof(float) * (2 * (size_t)c.chunk * c.swe_max + (size_t)c.band_cap * KT) +
                           sizeof(int) * ((size_t)c.band_cap + (size_t)c.pos_cap);
     c.raw_off = (int)((tables + 15) & ~(size_t)15);

@@ -17,8 +17,9 @@ namespace rs {
 //
 // Output index j of an axis of m outputs over n source samples maps to the
 // rational source coordinate x = num / den (Eq. 1 with scale = m / n):
-//   asymmetric: num = j n,            den = m
-//   half-pixel: num = (2j + 1) n - m, den = 2 m
+//   asymmetric:    num = j n,            den = m
+//   half-pixel:    num = (2j + 1) n - m, den = 2 m
+//   align-corners: num = j (n - 1),      den = m - 1  (num = 0, den = 1 if m = 1)
 // i0 = floor(x) and t = (num - i0 den) / den (Eqs. 2-4). The quotient is
 // estimated in FP32 (error < 1 for |num| < 2^34 and den <= 2^17) and then
 // corrected in exact 64-bit integer arithmetic, so i0 is exact and t takes a
@@ -39,18 +40,23 @@ __device__ __forceinline__ void axis_map(int j, int n, int m, int coord, int& i0
 {
     int64_t num, den;
     if (coord == COORD_ASYMMETRIC) { num = (int64_t)j * n; den = m; }
-    else { num = (int64_t)(2 * j + 1) * n - m; den = 2 * (int64_t)m; }
+    else if (coord == COORD_HALF_PIXEL) { num = (int64_t)(2 * j + 1) * n - m; den = 2 * (int64_t)m; }
+    else if (m > 1) { num = (int64_t)j * (n - 1); den = m - 1; }
+    else { num = 0; den = 1; }
     int64_t rem;
     i0 = floor_div_exact(num, den, rem);
     t = __fdiv_rn((float)rem, (float)den);
 }
 
-// Nearest sample: i0 (asymmetric, Eq. 2's x1) or floor(x + 1/2) (half-pixel).
+// Nearest sample: i0 (asymmetric, Eq. 2's x1) or floor(x + 1/2) (half-pixel,
+// align-corners).
 __device__ __forceinline__ int nearest_index(int j, int n, int m, int coord)
 {
     int64_t rem;
     if (coord == COORD_ASYMMETRIC) return floor_div_exact((int64_t)j * n, m, rem);
-    return floor_div_exact((int64_t)(2 * j + 1) * n, 2 * (int64_t)m, rem);
+    if (coord == COORD_HALF_PIXEL) return floor_div_exact((int64_t)(2 * j + 1) * n, 2 * (int64_t)m, rem);
+    if (m <= 1) return 0;
+    return floor_div_exact((int64_t)2 * j * (n - 1) + (m - 1), 2 * (int64_t)(m - 1), rem);
 }
 
 // Index of the first (unclamped) tap of output j for a KT-tap method:

@@ -8,7 +8,31 @@
 
 namespace rs {
 
-enum { COORD_ASYMMETRIC = 0, COORD_HALF_PIXEL = 1 };
+enum { COORD_ASYMMETRIC = 0, COORD_HALF_PIXEL = 1, COORD_ALIGN_CORNERS = 2 };
+
+// Advance of the mapped coordinate per output index, as the ratio an / am:
+// n / m (asymmetric, half-pixel), (n - 1) / (m - 1) (align-corners; 0 for
+// one output). first_tap(j + k - 1) - first_tap(j) <= ceil((k - 1) an / am).
+inline void coord_advance(int n, int m, int coord, int64_t& an, int64_t& am)
+{
+    if (coord == COORD_ALIGN_CORNERS) {
+        an = m > 1 ? n - 1 : 0;
+        am = m > 1 ? m - 1 : 1;
+    } else {
+        an = n;
+        am = m;
+    }
+}
+
+// Upper bound of first_tap(j + k - 1) - first_tap(j) + KT over all j: the
+// source span of k consecutive outputs with KT taps each.
+inline int tap_span_bound(int k, int n, int m, int KT, int coord)
+{
+    int64_t an, am;
+    coord_advance(n, m, coord, an, am);
+    const int64_t num = (int64_t)(k - 1) * an;
+    return (int)((num + am - 1) / am) + KT;
+}
 enum { DT_U8 = 0, DT_F16 = 1, DT_BF16 = 2, DT_F32 = 3 };
 enum { M_NEAREST = 0, M_BILINEAR = 1, M_BICUBIC = 2 };
 

@@ -480,12 +480,6 @@ k_stream(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Str
 // ---------------------------------------------------------------------------
 // Host side
 
-static int span_rows_bound(int k, int n, int m, int KT)
-{
-    const int64_t num = (int64_t)(k - 1) * n;
-    return (int)((num + m - 1) / m) + KT;
-}
-
 static int next_pow2(int v)
 {
     int p = 1;
@@ -509,11 +503,11 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
             (!planar || ((g.sp.n_stride * es) % 16 == 0 && (g.sp.c_stride * es) % 16 == 0)) ? 1 : 0;
     const int EPU = c.vec ? 16 / es : 1;
     const int kpx = (c.tile_w + g.C - 1) / g.C + 1;
-    const int span_px = span_rows_bound(kpx, g.W, g.Wo, KT);
+    const int span_px = tap_span_bound(kpx, g.W, g.Wo, KT, g.coord);
     // Unclamped footprint, the alignment margin of the first load unit (<
     // EPU) and the rounding of the row base to 4 elements (< 4).
     c.swe_max = ((span_px * g.C + 2 * EPU + 4) + 3) & ~3;
-    const int span_rows = span_rows_bound(c.chunk_h, g.H, g.Ho, KT);
+    const int span_rows = tap_span_bound(c.chunk_h, g.H, g.Ho, KT, g.coord);
     c.rh = next_pow2(span_rows);
     c.rs_rows = span_rows;
     // Band row table: at most kMaxBand rows (a multiple of chunk_h).

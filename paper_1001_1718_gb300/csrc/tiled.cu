@@ -19,15 +19,6 @@ k_tiled(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const Tile
 // ---------------------------------------------------------------------------
 // Host side
 
-static int span_bound(int k, int n, int m, int KT)
-{
-    // Largest (first tap of j + k - 1) - (first tap of j) + KT over all j:
-    // the mapped coordinate advances by (k - 1) n / m, so its floor by at
-    // most ceil((k - 1) n / m).
-    const int64_t num = (int64_t)(k - 1) * n;
-    return (int)((num + m - 1) / m) + KT;
-}
-
 bool tiled_config(const Geom& g, int method, TileCfg& cfg)
 {
     const int KT = method_taps(method);
@@ -36,8 +27,8 @@ bool tiled_config(const Geom& g, int method, TileCfg& cfg)
     const int nq = cfg.tile_w / 4;
     if (nq > cfg.threads || cfg.threads % nq) return false;
     const int kpx = (cfg.tile_w + g.C - 1) / g.C + 1;   // pixels a tile row can touch
-    cfg.sh_max = span_bound(cfg.tile_h, g.H, g.Ho, KT);
-    int swe = span_bound(kpx, g.W, g.Wo, KT) * g.C;
+    cfg.sh_max = tap_span_bound(cfg.tile_h, g.H, g.Ho, KT, g.coord);
+    int swe = tap_span_bound(kpx, g.W, g.Wo, KT, g.coord) * g.C;
     cfg.swe_max = (swe + 3) & ~3;
     cfg.smem = sizeof(float) * ((size_t)cfg.sh_max * cfg.swe_max + (size_t)cfg.sh_max * cfg.tile_w +
                                 (size_t)cfg.tile_h * KT) +

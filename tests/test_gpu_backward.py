@@ -8,7 +8,7 @@ import torch
 pytestmark = pytest.mark.gpu
 
 MN = {0: "nearest", 1: "bilinear", 2: "bicubic"}
-CN = {0: "asymmetric", 1: "half_pixel"}
+CN = {0: "asymmetric", 1: "half_pixel", 2: "align_corners"}
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +31,7 @@ SHAPES = [(37, 53, 74, 106), (64, 48, 32, 24), (31, 29, 53, 71), (40, 40, 40, 40
 
 
 @pytest.mark.parametrize("method", [0, 1, 2])
-@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("coord", [0, 1, 2])
 @pytest.mark.parametrize("impl", ["auto", "tiled"])
 def test_adjoint_nchw_matches_oracle(rs, oracle, method, coord, impl):
     for k, (H, W, Ho, Wo) in enumerate(SHAPES):
@@ -80,7 +80,7 @@ def test_autograd_function(rs, method):
 
 
 @pytest.mark.parametrize("method", [1, 2])
-@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("coord", [0, 1, 2])
 @pytest.mark.parametrize("scale", [2.0, 0.5])
 def test_against_central_differences(rs, oracle, method, coord, scale):
     """dL/dx of L = <resize(x), g> by FP64 central differences (eps = 1e-6)
@@ -158,15 +158,19 @@ def test_plane_groups_and_large_upscale(rs, oracle):
 # whole 16-byte units
 WIN_SHAPES = [(37, 54, 74, 108), (64, 48, 32, 24), (31, 29, 52, 56), (40, 40, 40, 40), (300, 258, 600, 516),
               (120, 90, 20, 12), (1, 17, 3, 32), (200, 150, 400, 300)]
+# align-corners steps by (n - 1) / (m - 1): x2 upscales give bicubic 9
+# transposed taps, so its shapes stay just below x2 (at most 8)
+WIN_SHAPES_ALIGN = [(37, 54, 70, 100), (64, 48, 32, 24), (31, 29, 52, 56), (40, 40, 40, 40), (300, 258, 560, 480),
+                    (120, 90, 20, 12), (1, 17, 3, 32), (200, 150, 370, 280)]
 
 
 @pytest.mark.parametrize("method", [0, 1, 2])
-@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("coord", [0, 1, 2])
 def test_window_adjoint(rs, oracle, method, coord):
     """The fused register-window adjoint (dY rows of whole 16-byte units, at
     most 8 transposed taps per axis) against the oracle's adjoint, and equal
     to the two-pass kernels, whose sums it runs in the same order."""
-    for k, (H, W, Ho, Wo) in enumerate(WIN_SHAPES):
+    for k, (H, W, Ho, Wo) in enumerate(WIN_SHAPES_ALIGN if coord == 2 else WIN_SHAPES):
         g = np.random.default_rng(300 + k).standard_normal((2, 3, Ho, Wo)).astype(np.float32)
         gt = torch.from_numpy(g).cuda()
         gi = rs.resize_backward(gt, (H, W), MN[method], layout="nchw", coord=CN[coord], impl="window")
@@ -177,16 +181,17 @@ def test_window_adjoint(rs, oracle, method, coord):
         tol = _tol(oracle, H, W, Ho, Wo, method, coord, np.abs(g).max())
         assert err <= tol, f"{MN[method]} {CN[coord]} {H}x{W}<-{Ho}x{Wo}: {err} > {tol}"
         assert torch.equal(gi, two), f"window vs two-pass {MN[method]} {CN[coord]} {H}x{W}<-{Ho}x{Wo}"
-    # interleaved channels
+    # interleaved channels (align-corners: just below x2, as above)
+    H, W = (47, 68) if coord == 2 else (45, 66)
     for C in (1, 3, 4):
         g = np.random.default_rng(9).standard_normal((90, 132, C)).astype(np.float32)
         gt = torch.from_numpy(g).cuda()
-        gi = rs.resize_backward(gt, (45, 66), MN[method], layout="hwc", coord=CN[coord], impl="window")
-        two = rs.resize_backward(gt, (45, 66), MN[method], layout="hwc", coord=CN[coord], impl="stream")
+        gi = rs.resize_backward(gt, (H, W), MN[method], layout="hwc", coord=CN[coord], impl="window")
+        two = rs.resize_backward(gt, (H, W), MN[method], layout="hwc", coord=CN[coord], impl="stream")
         torch.cuda.synchronize()
         assert torch.equal(gi, two)
-        ref = oracle.adjoint(g.astype(np.float64), 45, 66, method, coord)
-        assert np.abs(gi.cpu().numpy() - ref).max() <= _tol(oracle, 45, 66, 90, 132, method, coord, np.abs(g).max())
+        ref = oracle.adjoint(g.astype(np.float64), H, W, method, coord)
+        assert np.abs(gi.cpu().numpy() - ref).max() <= _tol(oracle, H, W, 90, 132, method, coord, np.abs(g).max())
     # not applicable: more than 8 transposed taps along x (bicubic x3), odd dY rows
     with pytest.raises(rs.ResampleError):
         rs.resize_backward(torch.randn(1, 1, 60, 60, device="cuda"), (20, 20), "bicubic", impl="window")

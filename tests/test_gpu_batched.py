@@ -55,6 +55,21 @@ def test_batched_matches_oracle_and_single(rs, oracle, dtype):
     assert rs.debug_fault() == 0
 
 
+@pytest.mark.parametrize("coord", ["half_pixel", "align_corners"])
+def test_batched_coordinate_maps(rs, oracle, coord):
+    """The batch under the other coordinate maps: each image equals the
+    single-image call with the same map and matches the oracle."""
+    srcs, sizes, methods, host = _batch(5, 12)
+    outs = rs.resize_batched(srcs, sizes, methods, coord=coord)
+    torch.cuda.synchronize()
+    code = {"half_pixel": 1, "align_corners": 2}[coord]
+    for x, s, m, y, h in zip(srcs, sizes, methods, outs, host):
+        assert torch.equal(rs.resize(x, s, m, coord=coord), y)
+        check(y, oracle.resize(h.astype(np.float64), s[0], s[1], rs.METHODS[m], code), "u8", rs.METHODS[m],
+              float(np.abs(h).max()), f"batched {coord} {m} {h.shape}->{s}")
+    assert rs.debug_fault() == 0
+
+
 def test_plan_replay(rs):
     srcs, sizes, methods, _ = _batch(4, 16)
     outs = [torch.zeros((h, w, x.shape[2]), dtype=torch.uint8, device="cuda") for x, (h, w) in zip(srcs, sizes)]

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 NN, BL, BC = 0, 1, 2
 MNAME = {NN: "nearest", BL: "bilinear", BC: "bicubic"}
-CNAME = {0: "asymmetric", 1: "half_pixel"}
+CNAME = {0: "asymmetric", 1: "half_pixel", 2: "align_corners"}
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +45,7 @@ SIZES = [
 
 
 @pytest.mark.parametrize("method", [NN, BL, BC])
-@pytest.mark.parametrize("coord", [0, 1])
+@pytest.mark.parametrize("coord", [0, 1, 2])
 @pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
 @pytest.mark.parametrize("C", [1, 3, 4])
 def test_hwc_all_sizes(rs, oracle, method, coord, dtype, C):
@@ -306,6 +306,51 @@ def test_window_shifted_staging(rs, oracle, dtype):
     assert rs.debug_fault() == 0
 
 
+def _unclamped_columns(n, m, method, coord):
+    """Output columns none of whose taps leave [0, n) (exact integer map)."""
+    K = 2 if method == BL else 4
+    keep = []
+    for j in range(m):
+        i0 = (j * n) // m if coord == 0 else ((2 * j + 1) * n - m) // (2 * m)
+        f = i0 - 1 if K == 4 else i0
+        if f >= 0 and f + K - 1 <= n - 1:
+            keep.append(j)
+    return keep
+
+
+@pytest.mark.parametrize("method", [NN, BL, BC])
+def test_align_corners_every_kernel(rs, oracle, method):
+    """The align-corners map through every forward kernel that takes the
+    method (explicit impl), against the oracle, and bit for bit against the
+    tiled kernel (same FP32 operations in the same order)."""
+    impls = ["plain", "tiled", "stream"] + (["gather"] if method == NN else ["window", "reduce"])
+    ran = {i: 0 for i in impls}
+    for k, (N, C, H, W, Ho, Wo) in enumerate([(2, 3, 75, 132, 150, 262), (1, 2, 96, 128, 37, 50),
+                                              (1, 1, 300, 516, 700, 1200), (1, 4, 9, 12, 1, 7)]):
+        for dtype in ("u8", "f32"):
+            t, x64 = _src(1900 + k, (N, C, H, W), dtype)
+            ref64 = oracle.resize_nchw(x64, Ho, Wo, method, 2)
+            tiled = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord="align_corners", impl="tiled")
+            for impl in impls:
+                if impl == "reduce" and dtype != "f32":
+                    continue
+                try:
+                    y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord="align_corners", impl=impl)
+                except rs.ResampleError:
+                    # the window kernel bounds the footprint of a whole 1024-element
+                    # strip, so it refuses strong downscales under any map
+                    assert impl == "window" and Ho < H, (impl, dtype, (H, W, Ho, Wo))
+                    continue
+                ran[impl] += 1
+                torch.cuda.synchronize()
+                check(y, ref64, dtype, method, np.abs(x64).max(),
+                      f"align {impl} {MNAME[method]} {dtype} {(N, C, H, W)}->{Ho}x{Wo}")
+                if impl != "reduce":
+                    assert torch.equal(y, tiled), (impl, dtype, (N, C, H, W, Ho, Wo))
+    assert all(v > 0 for v in ran.values()), ran
+    assert rs.debug_fault() == 0
+
+
 REDUCE_CASES = [
     # (N, C, H, W, Ho, Wo, coord); NCHW, W a multiple of 4
     (2, 3, 64, 80, 32, 40, 0),         # x0.5
@@ -330,6 +375,12 @@ def test_reduce_matches_oracle(rs, oracle, method):
         torch.cuda.synchronize()
         check(y, oracle.resize_nchw(x64, Ho, Wo, method, coord), "f32", method, np.abs(x64).max(),
               f"reduce nchw {MNAME[method]} {CNAME[coord]} {(N, C, H, W)}->{Ho}x{Wo}")
+        # Same FP32 operations in the same order as the tiled kernel (x taps,
+        # then y taps, ascending), except in columns whose x taps clamp onto
+        # an edge column, where REDUCE merges them: bit-equal elsewhere.
+        ref = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="tiled")
+        cols = _unclamped_columns(W, Wo, method, coord)
+        assert torch.equal(y[..., cols], ref[..., cols])
     for k, (H, W, C, Ho, Wo) in enumerate([(90, 128, 3, 45, 50), (256, 200, 3, 64, 52), (61, 77, 4, 30, 20)]):
         t, x64 = _src(1700 + k, (H, W, C), "f32")
         for coord in (0, 1):
