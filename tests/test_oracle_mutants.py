@@ -31,6 +31,8 @@ MUTANTS = {
     "f16_round_half_away": ("double r = nearbyint(d / q) * q;", "double r = round(d / q) * q;"),
     "nearest_half_pixel": ("i = floor_div((2 * j + 1) * n, 2 * m);",
                            "i = floor_div((2 * j + 1) * n - m, 2 * m);"),
+    "align_corners_denominator": ("        den = m - 1;\n", "        den = m;\n"),
+    "align_corners_nearest_floor": ("i = floor_div(2 * num + den, 2 * den);", "i = floor_div(2 * num, 2 * den);"),
 }
 
 
