@@ -7,30 +7,34 @@
 #include "capi_internal.h"
 #include "poly_body.cuh"
 
-// This file is compiled twice: as poly.cu (POLY_MODE 1, aligned staging,
-// plus the host configuration and launch) and through poly_shifted.cu
-// (POLY_MODE 2, shifted staging), so the two sets of kernels build in
-// parallel.
+// This file is compiled three times: as poly.cu (POLY_MODE 1, aligned
+// staging, plus the host configuration and launch), through poly_shifted.cu
+// (POLY_MODE 2, shifted staging) and through poly_x2.cu (POLY_MODE 1 with
+// POLY_FIX 2: exactly two output rows per source position), so the three
+// sets of kernels build in parallel.
 #ifndef POLY_MODE
 #define POLY_MODE 1
+#endif
+#ifndef POLY_FIX
+#define POLY_FIX 0
 #endif
 
 namespace rs {
 
-template <int KT, int C, typename T, int MODE>
+template <int KT, int C, typename T, int MODE, int FIX>
 __global__ void __launch_bounds__(kPolyThreads, 3)
 k_poly(const Geom g, const T* __restrict__ src, T* __restrict__ dst, const PolyCfg cfg, unsigned int* fault)
 {
     extern __shared__ __align__(16) float sm[];
     const int plane = blockIdx.z;
-    poly_body<KT, C, T, MODE>(g, src + g.sp.offset(plane), dst + g.dp.offset(plane), cfg, blockIdx.x, blockIdx.y,
+    poly_body<KT, C, T, MODE, FIX>(g, src + g.sp.offset(plane), dst + g.dp.offset(plane), cfg, blockIdx.x, blockIdx.y,
                               sm, fault);
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 
-#if POLY_MODE == 1
+#if POLY_MODE == 1 && POLY_FIX == 0
 bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c, bool shifted_only)
 {
     if (method != M_BILINEAR && method != M_BICUBIC) return false;
@@ -60,7 +64,7 @@ bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg&
 #endif
 
 template <int KT, int C, typename T>
-static void* poly_func(int) { return reinterpret_cast<void*>(&k_poly<KT, C, T, POLY_MODE>); }
+static void* poly_func(int) { return reinterpret_cast<void*>(&k_poly<KT, C, T, POLY_MODE, POLY_FIX>); }
 
 template <int KT, typename T>
 static void* poly_func_c(int C, int mode)
@@ -79,8 +83,9 @@ static void* poly_func_m(int method, int C, int mode)
     return method == M_BILINEAR ? poly_func_c<2, T>(C, mode) : poly_func_c<4, T>(C, mode);
 }
 
-#if POLY_MODE == 1
+#if POLY_MODE == 1 && POLY_FIX == 0
 void* poly_kernel_shifted(int method, int dtype, int C);   // poly_shifted.cu
+void* poly_kernel_x2(int method, int dtype, int C);        // poly_x2.cu
 static void* poly_kernel(int method, int dtype, int C, int mode)
 {
     if (mode == 2) return poly_kernel_shifted(method, dtype, C);
@@ -91,7 +96,7 @@ static void* poly_kernel(int method, int dtype, int C, int mode)
     default: return poly_func_m<float>(method, C, mode);
     }
 }
-#else
+#elif POLY_MODE == 2
 void* poly_kernel_shifted(int method, int dtype, int C)
 {
     switch (dtype) {
@@ -101,13 +106,28 @@ void* poly_kernel_shifted(int method, int dtype, int C)
     default: return poly_func_m<float>(method, C, 2);
     }
 }
+#else
+void* poly_kernel_x2(int method, int dtype, int C)
+{
+    switch (dtype) {
+    case DT_U8: return poly_func_m<uint8_t>(method, C, 1);
+    case DT_F16: return poly_func_m<__half>(method, C, 1);
+    case DT_BF16: return poly_func_m<__nv_bfloat16>(method, C, 1);
+    default: return poly_func_m<float>(method, C, 1);
+    }
+}
 #endif
 
-#if POLY_MODE == 1
+#if POLY_MODE == 1 && POLY_FIX == 0
 
 cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c, cudaStream_t st)
 {
-    void* func = poly_kernel(method, dtype, g.C, c.vec);
+    // The asymmetric map at exactly x2 vertically puts two output rows on
+    // every source position; bands of an even number of rows then start on
+    // an even row (the last band too: Ho is even), which the x2 kernels need.
+    const bool x2 = c.vec == 1 && g.coord == COORD_ASYMMETRIC && (int64_t)g.Ho == 2 * (int64_t)g.H &&
+                    (c.band_h <= 0 || c.band_h % 2 == 0);
+    void* func = x2 ? poly_kernel_x2(method, dtype, g.C) : poly_kernel(method, dtype, g.C, c.vec);
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
     if (e != cudaSuccess) return e;
     const int64_t strips = ((int64_t)g.Wo * g.C + kPolyElems - 1) / kPolyElems;
@@ -119,6 +139,7 @@ cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, v
         const int waves = c.waves > 0 ? c.waves : 2;
         const int64_t bands = std::max<int64_t>(1, (resident * waves + strips * g.planes - 1) / (strips * g.planes));
         c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.Ho + bands - 1) / bands));
+        if (x2 && c.band_h % 2) ++c.band_h;   // band_cap = min(256, Ho) is even here
     }
     if (c.band_h > c.band_cap) return cudaErrorInvalidValue;
     dim3 grid((unsigned)strips, (unsigned)((g.Ho + c.band_h - 1) / c.band_h), (unsigned)g.planes);

@@ -118,12 +118,17 @@ __device__ __forceinline__ float raw_to_float(float v) { return v; }
 
 // The work of one block: strip bx (1024 output elements) and band by of
 // one plane (s, d already point at the plane). Used by the single-image
-// kernel and by the persistent batched kernel.
-template <int KT, int C, typename T, int MODE>
+// kernel and by the persistent batched kernel. FIX = 2: every position of
+// the band emits exactly two output rows (the asymmetric map at exactly x2,
+// bands of an even number of rows from an even row), so the emit step needs
+// neither the per-position row count nor a loop; the block checks this
+// against its row taps and reports a fault instead of computing otherwise.
+template <int KT, int C, typename T, int MODE, int FIX = 0>
 __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s, T* __restrict__ d,
                                           const PolyCfg& cfg, int bx, int by, float* sm, unsigned int* fault)
 {
     static_assert(MODE == 1 || MODE == 2, "staging mode: 1 aligned units, 2 shifted blocks");
+    static_assert(FIX == 0 || FIX == 2, "rows per position: 0 any (table), 2 exactly two");
     const int tid = threadIdx.x;
 
     const int64_t WoC = (int64_t)g.Wo * C;
@@ -336,6 +341,15 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
             NC[RF[i0] - b_first] = len;
         }
     }
+    if constexpr (FIX == 2) {   // uniform; before any copy is issued
+        bool ok = (nrows % 2) == 0;
+        for (int q = tid; 2 * q < nrows; q += kPolyThreads)
+            ok = ok && RF[2 * q + 1] == RF[2 * q] && (2 * q + 2 >= nrows || RF[2 * q + 2] == RF[2 * q] + 1);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) report_fault(fault, FAULT_TILE_SRC_SPAN);
+            return;
+        }
+    }
     // Source rows in order: b_first .. b_last + KT - 1, in chunks of R.
     const int r_first = b_first, r_end = b_last + KT;      // [r_first, r_end)
     auto chunk_rows = [&](int c) { return max(0, min(R, r_end - (r_first + c * R))); };
@@ -397,21 +411,30 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     // Emit the output rows whose first tap is b (two at a time: independent
     // chains), from window slots slot[0..KT).
     auto emit = [&](const int* slot) {
-        const int nb = NC[b - b_first];
-        int k = 0;
-        for (; k + 1 < nb; k += 2) {
+        if constexpr (FIX == 2) {
             float2 a01, a23, c01, c23;
-            blend(i + k, slot, a01, a23);
-            blend(i + k + 1, slot, c01, c23);
-            put(i + k, a01, a23);
-            put(i + k + 1, c01, c23);
+            blend(i, slot, a01, a23);
+            blend(i + 1, slot, c01, c23);
+            put(i, a01, a23);
+            put(i + 1, c01, c23);
+            i += 2;
+        } else {
+            const int nb = NC[b - b_first];
+            int k = 0;
+            for (; k + 1 < nb; k += 2) {
+                float2 a01, a23, c01, c23;
+                blend(i + k, slot, a01, a23);
+                blend(i + k + 1, slot, c01, c23);
+                put(i + k, a01, a23);
+                put(i + k + 1, c01, c23);
+            }
+            if (k < nb) {
+                float2 a01, a23;
+                blend(i + k, slot, a01, a23);
+                put(i + k, a01, a23);
+            }
+            i += nb;
         }
-        if (k < nb) {
-            float2 a01, a23;
-            blend(i + k, slot, a01, a23);
-            put(i + k, a01, a23);
-        }
-        i += nb;
     };
 
     while (b <= b_last) {

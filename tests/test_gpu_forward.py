@@ -278,6 +278,36 @@ def test_gather_staged_rows(rs, oracle, dtype, band):
 
 
 @pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
+def test_window_exact_x2(rs, oracle, dtype):
+    """The register window at exactly x2 vertically under the asymmetric map
+    with 16-byte source rows (the kernels that emit two rows per source
+    position without the per-position table): several bands and strips,
+    both methods, chunks of 4 and 8 rows; against the oracle and bit for bit
+    against the tiled kernel. Near misses (2H + 1 rows, the half-pixel map)
+    take the general kernels and must agree the same way."""
+    cases = [((1, 3, 300, 256), (600, 512), 0), ((2, 1, 37, 64), (74, 100), 0), ((1, 4, 130, 48), (260, 96), 0),
+             ((1, 3, 300, 256), (601, 512), 0), ((1, 3, 300, 256), (600, 512), 1)]
+    for k, ((N, C, H, W), (Ho, Wo), coord) in enumerate(cases):
+        t, x64 = _src(2000 + k, (N, C, H, W), dtype)
+        for method in (BL, BC):
+            ref = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="tiled")
+            for chunk in (4, 8):
+                y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], layout="nchw", coord=CNAME[coord], impl="window",
+                              tile=(1024, chunk))
+                torch.cuda.synchronize()
+                assert torch.equal(y, ref), (dtype, (N, C, H, W), (Ho, Wo), coord, MNAME[method], chunk)
+            check(y, oracle.resize_nchw(x64, Ho, Wo, method, coord), dtype, method, np.abs(x64).max(),
+                  f"window x2 {dtype} {MNAME[method]} {(N, C, H, W)}->{Ho}x{Wo}")
+    # interleaved RGB, 16-byte rows, several strips
+    t, x64 = _src(2100, (120, 448, 3), dtype)
+    y = rs.resize(t.cuda(), (240, 1000), "bicubic", impl="window", tile=(1024, 8))
+    torch.cuda.synchronize()
+    assert torch.equal(y, rs.resize(t.cuda(), (240, 1000), "bicubic", impl="tiled"))
+    check(y, oracle.resize(x64, 240, 1000, BC, 0), dtype, BC, np.abs(x64).max(), f"window x2 hwc {dtype}")
+    assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
 def test_window_shifted_staging(rs, oracle, dtype):
     """The register-window kernel on source rows that are not whole 16-byte
     units (odd widths, NCHW planes starting mid-unit, a pitched view whose
