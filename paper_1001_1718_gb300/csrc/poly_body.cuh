@@ -411,7 +411,18 @@ __device__ __forceinline__ void poly_body(const Geom& g, const T* __restrict__ s
     // Emit the output rows whose first tap is b (two at a time: independent
     // chains), from window slots slot[0..KT).
     auto emit = [&](const int* slot) {
-        if constexpr (FIX == 2) {
+        if constexpr (FIX == 2 && std::is_same<T, uint8_t>::value) {
+            // The band starts on an even row, so row i has t = 0 and the
+            // weights (0, 1, 0, 0) (bilinear (1, 0)); with finite values (all
+            // uint8 data) the blend returns the window row itself, up to the
+            // sign of a zero, which the byte conversion does not see.
+            constexpr int s1 = KT == 4 ? 1 : 0;
+            float2 c01, c23;
+            blend(i + 1, slot, c01, c23);
+            put(i, h01[slot[s1]], h23[slot[s1]]);
+            put(i + 1, c01, c23);
+            i += 2;
+        } else if constexpr (FIX == 2) {
             float2 a01, a23, c01, c23;
             blend(i, slot, a01, a23);
             blend(i + 1, slot, c01, c23);
