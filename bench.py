@@ -166,7 +166,7 @@ class ClockSampler:
 # Source files each profiled kernel is built from (a change to any of them
 # voids its recorded DRAM traffic).
 KERNEL_SOURCES = {
-    "k_poly": ["poly.cu", "poly_body.cuh", "rs_common.cuh", "rs_internal.h"],
+    "k_poly": ["poly.cu", "poly_x2.cu", "poly_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_stream": ["stream.cu", "rs_common.cuh", "rs_internal.h"],
     "k_tiled": ["tiled.cu", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_nearest": ["nearest.cu", "rs_common.cuh", "rs_internal.h"],
