@@ -809,6 +809,17 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// A forward problem in the window pass's adjoint roles: "dY" (Ho x Wo
+// there) is the source image, "dX" (H x W) the output.
+static Geom forward_as_adjoint(const Geom& gf)
+{
+    Geom g = gf;
+    g.H = gf.Ho; g.W = gf.Wo; g.Ho = gf.H; g.Wo = gf.W;
+    g.sp = gf.dp; g.dp = gf.sp;
+    g.src_pitch = gf.dst_pitch; g.dst_pitch = gf.src_pitch;
+    return g;
+}
+
 // Host ranges of the antialias taps (the same integer bounds as the kernel).
 static AxisRanges aa_ranges(int n, int m, int method)
 {
@@ -831,12 +842,7 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
     if (dtype != DT_F32) return RS_ERR_UNSUPPORTED;
     if (method != M_BILINEAR && method != M_BICUBIC) return RS_ERR_INVALID_ARG;
     if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) return RS_ERR_INVALID_ARG;
-    // The fused window pass in its adjoint roles: "dY" (Ho x Wo there) is the
-    // source image, "dX" (H x W) the output.
-    Geom g = gf;
-    g.H = gf.Ho; g.W = gf.Wo; g.Ho = gf.H; g.Wo = gf.W;
-    g.sp = gf.dp; g.dp = gf.sp;
-    g.src_pitch = gf.dst_pitch; g.dst_pitch = gf.src_pitch;
+    const Geom g = forward_as_adjoint(gf);
     BwdPlan p;
     p.ry = aa_ranges(gf.H, gf.Ho, method);
     p.rx = aa_ranges(gf.W, gf.Wo, method);
@@ -874,10 +880,7 @@ static AxisRanges point_ranges(int n, int m, int method, int coord, bool columns
 static bool reduce_setup(const Geom& gf, int method, int dtype, const void* src, Geom& g, BwdPlan& p, AdjWinCfg& c)
 {
     if (dtype != DT_F32 || (method != M_BILINEAR && method != M_BICUBIC)) return false;
-    g = gf;
-    g.H = gf.Ho; g.W = gf.Wo; g.Ho = gf.H; g.Wo = gf.W;
-    g.sp = gf.dp; g.dp = gf.sp;
-    g.src_pitch = gf.dst_pitch; g.dst_pitch = gf.src_pitch;
+    g = forward_as_adjoint(gf);
     p.ry = point_ranges(gf.H, gf.Ho, method, gf.coord, false);
     p.rx = point_ranges(gf.W, gf.Wo, method, gf.coord, true);
     p.yK = p.xK = method_taps(method);
