@@ -281,15 +281,23 @@ k_nearest_rows(const Geom g, const T* __restrict__ src, T* __restrict__ dst, int
         #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = __byte_perm(W[wa[q]], W[wb[q]], sel[q]);
         const int i_end = pos_i[p + 1];
-        for (int i = pos_i[p]; i < i_end; ++i) {
-            unsigned char* out = dband + i * pitch_b;
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int wo = 4 * (tid + kNnThreads * q);
-                if (wo + 4 <= nb) {
-                    *reinterpret_cast<uint32_t*>(out + wo) = v[q];
-                } else if (wo < nb) {
-                    for (int k = 0; k < nb - wo; ++k) out[wo + k] = (unsigned char)(v[q] >> (8 * k));
+        if (nb == kNnStripBytes) {   // uniform: a full strip, every word in range
+            for (int i = pos_i[p]; i < i_end; ++i) {
+                uint32_t* out = reinterpret_cast<uint32_t*>(dband + i * pitch_b) + tid;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) out[kNnThreads * q] = v[q];
+            }
+        } else {
+            for (int i = pos_i[p]; i < i_end; ++i) {
+                unsigned char* out = dband + i * pitch_b;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int wo = 4 * (tid + kNnThreads * q);
+                    if (wo + 4 <= nb) {
+                        *reinterpret_cast<uint32_t*>(out + wo) = v[q];
+                    } else if (wo < nb) {
+                        for (int k = 0; k < nb - wo; ++k) out[wo + k] = (unsigned char)(v[q] >> (8 * k));
+                    }
                 }
             }
         }
