@@ -436,10 +436,24 @@ def run_e2e(torch, rs, img, outs, dev, stream, steps, warmup):
             "d2h_bytes_per_step": int(sum(t.numel() for t in host_out.values()))}
 
 
-def cpu_baseline(oracle, img, budget_s=8.0, band=64):
+def cpu_baseline(oracle, img, budget_s=8.0, band=64, single_s=2.0):
     """The FP64 oracle on this host's cores on a bounded sample of the step:
     bands of `band` output rows of each of the three outputs, round robin,
-    until `budget_s` seconds of wall time have been spent."""
+    until `budget_s` seconds of wall time have been spent; then the same on
+    one thread for `single_s` seconds (reported beside it)."""
+    line = _oracle_sample(oracle, img, budget_s, band)
+    if single_s > 0:
+        cores = oracle.num_threads()
+        oracle.set_num_threads(1)
+        try:
+            one = _oracle_sample(oracle, img, single_s, band)
+        finally:
+            oracle.set_num_threads(cores)
+        line["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": 1, "sample": one["sample"]}
+    return line
+
+
+def _oracle_sample(oracle, img, budget_s, band):
     x = img.astype(np.float64)
     H, W, C = img.shape
     jobs = []
