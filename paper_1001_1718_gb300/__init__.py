@@ -105,8 +105,31 @@ def _out_shape(x: torch.Tensor, layout: str, Ho: int, Wo: int) -> tuple:
     return tuple(sh)
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(t: torch.Tensor) -> int:
+    """torch's current stream on t's device, as a raw cudaStream_t."""
+    if _raw_stream is not None:
+        return _raw_stream(t.device.index)
     return torch.cuda.current_stream(t.device).cuda_stream
+
+
+class _on_device:
+    """Makes t's device current for the library call (the library launches on
+    the current device), entering torch's device context only when another
+    device is current."""
+
+    def __init__(self, t: torch.Tensor):
+        self.ctx = None if t.device.index == torch.cuda.current_device() else torch.cuda.device(t.device)
+
+    def __enter__(self):
+        if self.ctx is not None:
+            self.ctx.__enter__()
+
+    def __exit__(self, *exc):
+        if self.ctx is not None:
+            self.ctx.__exit__(*exc)
 
 
 def _opts(coord, cubic_a, impl, tile, threads, waves=0) -> B.RsOptions:
@@ -136,7 +159,7 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
     o = _opts(coord, cubic_a, impl, tile, threads, waves)
     if antialias:
         o.flags = B.RS_FLAG_ANTIALIAS
-    with torch.cuda.device(x.device):
+    with _on_device(x):
         B.check(lib().rs_resize_ex(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo),
                                    _dtype(x), _code(METHODS, method, "method"), ctypes.byref(o),
                                    _stream(x)), "rs_resize_ex")

@@ -117,10 +117,19 @@ def check(status: int, where: str) -> None:
         raise ResampleError(status, where)
 
 
+_default_options = None
+
+
 def options(coord: int = RS_COORD_ASYMMETRIC, cubic_a: float = -0.5, impl: int = RS_IMPL_AUTO,
             tile_w: int = 0, tile_h: int = 0, threads: int = 0, waves: int = 0) -> RsOptions:
-    o = RsOptions()
-    lib().rs_options_init(ctypes.byref(o))
+    """rs_options with the library's defaults (rs_options_init, called once)
+    and the given fields."""
+    global _default_options
+    if _default_options is None:
+        d = RsOptions()
+        lib().rs_options_init(ctypes.byref(d))
+        _default_options = bytes(d)
+    o = RsOptions.from_buffer_copy(_default_options)
     o.coord, o.cubic_a, o.impl = coord, cubic_a, impl
     o.tile_w, o.tile_h, o.threads, o.waves = tile_w, tile_h, threads, waves
     return o

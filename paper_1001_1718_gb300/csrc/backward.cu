@@ -793,10 +793,8 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
     if (c.nt != kAwThreads && (c.nt != 128 || tm == TAPS_TABLE)) return cudaErrorInvalidValue;
     void* func = g.C == 1 ? adj_window_fx<1>(KX, KY, tm, c.nt) : g.C == 2 ? adj_window_fx<2>(KX, KY, tm, c.nt)
                : g.C == 3 ? adj_window_fx<3>(KX, KY, tm, c.nt) : adj_window_fx<4>(KX, KY, tm, c.nt);
-    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, c.nt, c.smem);
+    cudaError_t e = prepare_kernel(func, c.smem, c.nt, &per_sm);
     if (e != cudaSuccess) return e;
     const int64_t strips = ((int64_t)g.W * g.C + 2 * c.nt - 1) / (2 * c.nt);
     const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
@@ -915,7 +913,7 @@ static cudaError_t launch_adj(const Geom& g, const float* dY, float* dX, const A
                               cudaStream_t st)
 {
     auto kern = k_adjoint<KX, C>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kern), cfg.smem, cfg.tile_w * cfg.ty, nullptr);
     if (e != cudaSuccess) return e;
     dim3 block(cfg.tile_w, cfg.ty);
     dim3 grid((unsigned)(((int64_t)g.W * C + cfg.tile_w - 1) / cfg.tile_w), (unsigned)((g.H + cfg.tile_h - 1) / cfg.tile_h),

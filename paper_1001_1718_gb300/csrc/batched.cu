@@ -415,10 +415,8 @@ static cudaError_t class_launches(const BatchLayout& L, int dtype, const rs_opti
         ClassLaunch& cl = out[nl++];
         cl.func = class_func(dtype, c);
         const int threads = c == kTileClass ? L.threads : 256;
-        cudaError_t e = cudaFuncSetAttribute(cl.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem[c]);
-        if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cl.func, threads, L.smem[c]);
+        cudaError_t e = prepare_kernel(cl.func, L.smem[c], threads, &per_sm);
         if (e != cudaSuccess) return e;
         const int64_t blocks = std::min<int64_t>(L.total[c], (int64_t)num_sms() * std::max(1, per_sm));
         cl.grid = dim3((unsigned)std::max<int64_t>(1, blocks));

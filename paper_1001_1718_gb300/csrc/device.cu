@@ -2,7 +2,9 @@
 // The fault word is a static __device__ variable; host code must not use its
 // name as a device address, so its address is resolved per device with
 // cudaGetSymbolAddress (with that device current) and passed to kernels.
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "rs_internal.h"
 
@@ -51,6 +53,37 @@ size_t max_smem_per_block()
         g_smem[dev] = (size_t)v;
     }
     return g_smem[dev];
+}
+
+// Dynamic shared-memory limits already raised, per (device, kernel), and
+// resident blocks per SM, per (device, kernel, threads, bytes): each driver
+// query runs once, not on every launch.
+static std::map<std::pair<int, const void*>, size_t> g_smem_set;
+static std::map<std::tuple<int, const void*, int, size_t>, int> g_occupancy;
+
+cudaError_t prepare_kernel(const void* func, size_t smem, int threads, int* per_sm)
+{
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    size_t& set = g_smem_set[{dev, func}];
+    if (smem > set) {
+        const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    if (per_sm) {
+        const auto key = std::make_tuple(dev, func, threads, smem);
+        auto it = g_occupancy.find(key);
+        if (it == g_occupancy.end()) {
+            int v = 0;
+            const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, func, threads, smem);
+            if (e != cudaSuccess) return e;
+            it = g_occupancy.emplace(key, v).first;
+        }
+        *per_sm = it->second;
+    }
+    return cudaSuccess;
 }
 
 int num_sms()

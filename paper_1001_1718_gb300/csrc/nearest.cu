@@ -432,7 +432,7 @@ cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst,
         const size_t smem = (size_t)kNnSlots * span_units * 16 + sizeof(int) * (3 * (size_t)band + 1);
         if (smem <= max_smem_per_block()) {
             void* func = nn_rows_kernel(dtype, g.C);
-            cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = prepare_kernel(func, smem, kNnThreads, nullptr);
             if (e != cudaSuccess) return e;
             const int64_t es = (int64_t)dtype_size(dtype);
             dim3 grid((unsigned)(((int64_t)g.Wo * g.C * es + kNnStripBytes - 1) / kNnStripBytes),

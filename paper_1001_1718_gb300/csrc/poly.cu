@@ -128,13 +128,11 @@ cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, v
     const bool x2 = c.vec == 1 && g.coord == COORD_ASYMMETRIC && (int64_t)g.Ho == 2 * (int64_t)g.H &&
                     (c.band_h <= 0 || c.band_h % 2 == 0);
     void* func = x2 ? poly_kernel_x2(method, dtype, g.C) : poly_kernel(method, dtype, g.C, c.vec);
-    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    int per_sm = 1;
+    cudaError_t e = prepare_kernel(func, c.smem, kPolyThreads, c.band_h <= 0 ? &per_sm : nullptr);
     if (e != cudaSuccess) return e;
     const int64_t strips = ((int64_t)g.Wo * g.C + kPolyElems - 1) / kPolyElems;
     if (c.band_h <= 0) {
-        int per_sm = 1;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kPolyThreads, c.smem);
-        if (e != cudaSuccess) return e;
         const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
         const int waves = c.waves > 0 ? c.waves : 2;
         const int64_t bands = std::max<int64_t>(1, (resident * waves + strips * g.planes - 1) / (strips * g.planes));

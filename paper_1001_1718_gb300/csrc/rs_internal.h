@@ -108,6 +108,10 @@ size_t dtype_size(int dtype);
 // Maximum dynamic shared memory a block may use on this device.
 size_t max_smem_per_block();
 int num_sms();
+// Raises func's dynamic shared-memory limit to at least smem bytes and, if
+// per_sm is given, returns its resident blocks per SM at `threads` threads
+// and smem bytes; both driver queries are cached per device and kernel.
+cudaError_t prepare_kernel(const void* func, size_t smem, int threads, int* per_sm);
 
 // Fault word of the current device (a static __device__ word resolved by
 // cudaGetSymbolAddress), or nullptr if it cannot be resolved.

@@ -570,12 +570,10 @@ cudaError_t launch_stream(const Geom& g, int method, int dtype, const void* src,
                           cudaStream_t st)
 {
     void* func = stream_kernel(method, dtype, g.C);
-    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    int per_sm = 1;
+    cudaError_t e = prepare_kernel(func, c.smem, kThreads, c.band_h <= 0 ? &per_sm : nullptr);
     if (e != cudaSuccess) return e;
     if (c.band_h <= 0) {
-        int per_sm = 1;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kThreads, c.smem);
-        if (e != cudaSuccess) return e;
         c.band_h = choose_band(g, c, per_sm, c.waves > 0 ? c.waves : 4);
     }
     dim3 grid((unsigned)(((int64_t)g.Wo * g.C + c.tile_w - 1) / c.tile_w),

@@ -62,8 +62,7 @@ static cudaError_t launch_t(const Geom& g, const void* src, void* dst, const Til
                             cudaStream_t st)
 {
     auto kern = k_tiled<KT, C, T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cfg.smem);
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kern), cfg.smem, cfg.threads, nullptr);
     if (e != cudaSuccess) return e;
     const int64_t WoC = (int64_t)g.Wo * C;
     dim3 grid((unsigned)((WoC + cfg.tile_w - 1) / cfg.tile_w),
