@@ -197,7 +197,7 @@ def resize_backward(grad_out: torch.Tensor, in_hw, method="bilinear", *, layout:
                                                ctypes.byref(n)), "rs_resize_backward_workspace")
     if workspace is None or workspace.numel() * workspace.element_size() < n.value:
         workspace = torch.empty(max(1, n.value), dtype=torch.uint8, device=grad_out.device)
-    with torch.cuda.device(grad_out.device):
+    with _on_device(grad_out):
         B.check(lib().rs_resize_backward(grad_out.data_ptr(), ctypes.byref(Lo), grad_in.data_ptr(),
                                          ctypes.byref(Li), _dtype(grad_out), m, ctypes.byref(o),
                                          workspace.data_ptr(), n.value, _stream(grad_out)),
@@ -264,7 +264,7 @@ def resize_batched(srcs: Sequence[torch.Tensor], sizes, methods, *, coord="asymm
     if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
     o = _opts(coord, cubic_a, impl, tile, threads)
-    with torch.cuda.device(srcs[0].device):
+    with _on_device(srcs[0]):
         B.check(lib().rs_resize_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),
                                         _stream(srcs[0])), "rs_resize_batched")
     return outs
@@ -318,7 +318,7 @@ def autotune(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric",
     Li, Lo = _layout(x, layout), _layout(out, layout)
     o = _opts(coord, cubic_a, "auto", None, 0)
     best = B.RsTileConfig()
-    with torch.cuda.device(x.device):
+    with _on_device(x):
         B.check(lib().rs_autotune(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo), _dtype(x),
                                   _code(METHODS, method, "method"), ctypes.byref(o), _stream(x),
                                   ctypes.byref(best)), "rs_autotune")
@@ -340,7 +340,7 @@ def autotune_batched(srcs, outs, methods, *, coord="asymmetric", cubic_a: float 
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
     o = _opts(coord, cubic_a, "auto", None, 0)
     best = B.RsTileConfig()
-    with torch.cuda.device(srcs[0].device):
+    with _on_device(srcs[0]):
         B.check(lib().rs_autotune_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),
                                           _stream(srcs[0]), ctypes.byref(best)), "rs_autotune_batched")
     return {"impl": IMPL_NAMES.get(best.impl, best.impl), "band": best.tile_w, "chunk": best.tile_h,
