@@ -75,6 +75,36 @@ def test_validation_rejects_before_any_launch(L):
     assert L.rs_resize(P, 16, 16, 1, B.RS_U8, P + 100, 8, 8, B.RS_BILINEAR, None) == B.RS_ERR_INVALID_ARG
 
 
+def test_coordinate_map_and_impl_options(L):
+    """The three coordinate maps are accepted and others refused; RS_IMPL_REDUCE
+    is refused for what it does not cover (host logic: no buffers needed)."""
+    import ctypes
+    from paper_1001_1718_gb300 import _binding as B
+    Li, Lo = L.rs_layout_nchw(2, 3, 64, 80), L.rs_layout_nchw(2, 3, 32, 40)
+    c = B.RsTileConfig()
+    for coord in (B.RS_COORD_ASYMMETRIC, B.RS_COORD_HALF_PIXEL, B.RS_COORD_ALIGN_CORNERS):
+        o = B.options(coord=coord)
+        assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, B.RS_BICUBIC, ctypes.byref(o),
+                                    ctypes.byref(c)) == 0
+    for coord in (-1, 3):
+        o = B.options(coord=coord)
+        assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, B.RS_BICUBIC, ctypes.byref(o),
+                                    ctypes.byref(c)) == B.RS_ERR_INVALID_ARG
+    o = B.options(impl=B.RS_IMPL_REDUCE + 1)
+    assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, B.RS_BILINEAR, ctypes.byref(o),
+                                ctypes.byref(c)) == B.RS_ERR_INVALID_ARG
+    o = B.options(impl=B.RS_IMPL_REDUCE)
+    assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), B.RS_F32, B.RS_BILINEAR, ctypes.byref(o),
+                                ctypes.byref(c)) == 0 and c.impl == B.RS_IMPL_REDUCE
+    for dt, m in ((B.RS_U8, B.RS_BILINEAR), (B.RS_F16, B.RS_BICUBIC), (B.RS_F32, B.RS_NEAREST)):
+        assert L.rs_tile_config_for(ctypes.byref(Li), ctypes.byref(Lo), dt, m, ctypes.byref(o),
+                                    ctypes.byref(c)) == B.RS_ERR_INVALID_ARG
+    # rows of 63 FP32 elements are not whole 16-byte units
+    Lr, Lro = L.rs_layout_nchw(1, 1, 64, 63), L.rs_layout_nchw(1, 1, 32, 32)
+    assert L.rs_tile_config_for(ctypes.byref(Lr), ctypes.byref(Lro), B.RS_F32, B.RS_BILINEAR, ctypes.byref(o),
+                                ctypes.byref(c)) == B.RS_ERR_INVALID_ARG
+
+
 def test_layout_validation(L):
     from paper_1001_1718_gb300 import _binding as B
     P, Q = 0x10000, 0x90000000
