@@ -79,6 +79,7 @@ cudaError_t prepare_kernel(const void* func, size_t smem, int threads, int* per_
             int v = 0;
             const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, func, threads, smem);
             if (e != cudaSuccess) return e;
+            if (g_occupancy.size() >= 4096) g_occupancy.clear();   // many shapes: start over
             it = g_occupancy.emplace(key, v).first;
         }
         *per_sm = it->second;
