@@ -304,9 +304,11 @@ rs_status rs_batched_plan_launch(rs_batched_plan* plan, void* stream);
 rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
 
 /*
- * Autotuner. A configuration is a kernel (STREAM or TILED) and its shape:
- * STREAM strip width tile_w x chunk height tile_h with `waves` blocks per
- * resident slot; TILED tile_w elements x tile_h rows with `threads` threads.
+ * Autotuner. A configuration is a kernel and its shape: WINDOW chunk height
+ * tile_h with `waves` blocks per resident slot; STREAM strip width tile_w x
+ * chunk height tile_h with `waves`; TILED tile_w elements x tile_h rows with
+ * `threads` threads; GATHER (nearest) strip width x rows; REDUCE (FP32,
+ * no shape).
  * rs_autotune times every candidate configuration on the caller's buffers
  * (dst is overwritten; the stream is synchronised while it runs) and stores
  * the fastest in the in-process cache, keyed by GPU, dtype, method, channel
@@ -314,7 +316,7 @@ rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
  * The cache can be saved to and loaded from a text file.
  */
 typedef struct {
-    int32_t impl;       /* RS_IMPL_WINDOW, RS_IMPL_STREAM, RS_IMPL_TILED or RS_IMPL_GATHER */
+    int32_t impl;       /* RS_IMPL_WINDOW, RS_IMPL_REDUCE, RS_IMPL_STREAM, RS_IMPL_TILED or RS_IMPL_GATHER */
     int32_t tile_w, tile_h, threads, waves;
     float best_us;      /* measured time of the chosen configuration */
     float default_us;   /* measured time of the default configuration */
