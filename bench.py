@@ -38,7 +38,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "output Gpixels/s and % of HBM roofline, batched/low-precision vs plain FP32, at stated error"
 HEADLINE_OPS = (("bicubic_x2", "bicubic", 2.0), ("bicubic_x1.7", "bicubic", 1.7), ("nearest_x2", "nearest", 2.0))
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_NAMES = {"window": "k_poly", "stream": "k_stream", "tiled": "k_tiled", "gather": "k_nearest",
+KERNEL_NAMES = {"window": "k_win", "stream": "k_stream", "tiled": "k_tiled", "gather": "k_nearest",
                 "plain": "k_plain"}
 
 
@@ -166,7 +166,7 @@ class ClockSampler:
 # Source files each profiled kernel is built from (a change to any of them
 # voids its recorded DRAM traffic).
 KERNEL_SOURCES = {
-    "k_poly": ["poly.cu", "poly_x2.cu", "poly_body.cuh", "rs_common.cuh", "rs_internal.h"],
+    "k_win": ["win.cu", "win_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_stream": ["stream.cu", "rs_common.cuh", "rs_internal.h"],
     "k_tiled": ["tiled.cu", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_nearest": ["nearest.cu", "rs_common.cuh", "rs_internal.h"],

@@ -104,10 +104,10 @@ static bool make_choice(const Geom& g, int method, int dtype, const void* src, c
         return method == RS_NEAREST && nearest_config(g, dtype, t.tile_w, t.tile_h);
     }
     if (t.impl == RS_IMPL_WINDOW) {
-        k.window = PolyCfg{};
+        k.window = WinCfg{};
         k.window.chunk = t.tile_h;
         k.window.waves = t.waves;
-        return poly_config(g, method, dtype, src, k.window);
+        return win_config(g, method, dtype, k.window);
     }
     if (t.impl == RS_IMPL_REDUCE) return reduce_config(g, method, dtype, src, nullptr);
     if (t.impl == RS_IMPL_STREAM) {
@@ -146,8 +146,8 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
     }
     if ((g.Ho >= g.H || dtype == DT_U8) && out_elems >= (int64_t)1 << 22) {
         for (int ch : {8, 4}) {
-            const Tuned t{RS_IMPL_WINDOW, 1024, ch, 256, 2};
-            if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= (ch == 8 ? 72 : 100) * 1024) return true;
+            const Tuned t{RS_IMPL_WINDOW, 1024, ch, 128, 2};
+            if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= (ch == 8 ? 56 : 100) * 1024) return true;
         }
     }
     StreamCfg sc = stream_default(g, method, dtype, src);
@@ -174,7 +174,7 @@ rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, c
         return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
     }
     if (o.impl == RS_IMPL_WINDOW) {
-        const Tuned t{RS_IMPL_WINDOW, 1024, o.tile_h ? o.tile_h : 8, 256, o.waves ? o.waves : 2};
+        const Tuned t{RS_IMPL_WINDOW, 1024, o.tile_h ? o.tile_h : 8, 128, o.waves ? o.waves : 2};
         return make_choice(g, method, dtype, src, t, k) ? RS_OK : RS_ERR_INVALID_ARG;
     }
     if (o.impl == RS_IMPL_REDUCE) {
@@ -212,7 +212,7 @@ cudaError_t launch_choice(const Geom& g, int method, int dtype, const void* src,
                           cudaStream_t st)
 {
     if (k.impl == RS_IMPL_GATHER) return launch_nearest(g, dtype, src, dst, k.gather_w, k.gather_rows, st);
-    if (k.impl == RS_IMPL_WINDOW) return launch_poly(g, method, dtype, src, dst, k.window, st);
+    if (k.impl == RS_IMPL_WINDOW) return launch_win(g, method, dtype, src, dst, k.window, st);
     if (k.impl == RS_IMPL_STREAM) return launch_stream(g, method, dtype, src, dst, k.stream, st);
     if (k.impl == RS_IMPL_REDUCE) return launch_reduce(g, method, dtype, src, dst, st);
     return launch_tiled(g, method, dtype, src, dst, k.tile, st);
@@ -249,7 +249,7 @@ static cudaError_t time_choice(const Geom& g, int method, int dtype, const void*
 static Tuned to_tuned(const KernelChoice& k)
 {
     if (k.impl == RS_IMPL_GATHER) return Tuned{RS_IMPL_GATHER, k.gather_w, k.gather_rows, 256, 0};
-    if (k.impl == RS_IMPL_WINDOW) return Tuned{RS_IMPL_WINDOW, 1024, k.window.chunk, 256, k.window.waves};
+    if (k.impl == RS_IMPL_WINDOW) return Tuned{RS_IMPL_WINDOW, 1024, k.window.chunk, 128, k.window.waves};
     if (k.impl == RS_IMPL_STREAM) return Tuned{RS_IMPL_STREAM, k.stream.tile_w, k.stream.chunk_h, 256, k.stream.waves};
     if (k.impl == RS_IMPL_REDUCE) return Tuned{RS_IMPL_REDUCE, 0, 0, 256, 0};
     return Tuned{RS_IMPL_TILED, k.tile.tile_w, k.tile.tile_h, k.tile.threads, 0};
@@ -281,7 +281,7 @@ rs_status rs_autotune(const void* src, const rs_layout* in, void* dst, const rs_
     std::vector<Tuned> cands;
     cands.push_back(Tuned{RS_IMPL_REDUCE, 0, 0, 256, 0});
     for (int ch : {4, 8, 16})
-        for (int wv : {1, 2, 4}) cands.push_back(Tuned{RS_IMPL_WINDOW, 1024, ch, 256, wv});
+        for (int wv : {1, 2, 4}) cands.push_back(Tuned{RS_IMPL_WINDOW, 1024, ch, 128, wv});
     for (int tw : {128, 256, 512, 1024})
         for (int ch : {4, 8, 16, 32})
             for (int wv : {2, 4, 8}) cands.push_back(Tuned{RS_IMPL_STREAM, tw, ch, 256, wv});

@@ -24,7 +24,7 @@
 #include <vector>
 
 #include "capi_internal.h"
-#include "poly_body.cuh"
+#include "win_body.cuh"
 #include "tile_body.cuh"
 
 namespace rs {
@@ -36,17 +36,17 @@ struct BatchImage {
     int H, W, Ho, Wo;
     int C, method, tiles_x, kind;          // tiles_x: items per row of items; kind 0 tile, 1 window
     int tile_w, tile_h, sh_max, swe_max;   // kind 0: tiled-kernel tile
-    int chunk, band_h, w_swe_max, band_cap, pos_cap, vec, raw_row, raw_off;   // kind 1: window config
+    int chunk, band_h, swe, raw_row, band_cap, pos_cap, tab_off, raw_off;   // kind 1: window config
 };
 
 // Classes: 0..7 = window (KT 2 / 4) x (C 1..4) with a footprint of at most
-// kWindowSmallSmem bytes of shared memory (three blocks per SM), 8..15 the
+// kWindowSmallSmem bytes of shared memory (four blocks per SM), 8..15 the
 // same with larger footprints (up to ~100 KB, two blocks per SM), 16 =
 // tiled. Splitting by footprint keeps one large image from lowering the
 // occupancy of its whole class.
 static constexpr int kClasses = 17;
 static constexpr int kTileClass = 16;
-static constexpr size_t kWindowSmallSmem = 72 * 1024;
+static constexpr size_t kWindowSmallSmem = 56 * 1024;
 
 __device__ __forceinline__ int find_image(const int64_t* __restrict__ start, int n, int64_t t)
 {
@@ -74,7 +74,7 @@ __device__ __forceinline__ Geom image_geom(const BatchImage& im, int coord, floa
 
 // Window items of one (KT, C) class.
 template <int KT, int C, typename T>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(kWinThreads, 2)
 k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start, int n, int64_t total,
                  int coord, float a, unsigned int* fault)
 {
@@ -88,19 +88,19 @@ k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict_
             continue;
         }
         const Geom g = image_geom(im, coord, a);
-        PolyCfg pc;
-        pc.chunk = im.chunk;
-        pc.band_h = im.band_h;
-        pc.waves = 0;
-        pc.swe_max = im.w_swe_max;
-        pc.band_cap = im.band_cap;
-        pc.pos_cap = im.pos_cap;
-        pc.vec = im.vec;
-        pc.raw_row = im.raw_row;
-        pc.raw_off = im.raw_off;
-        pc.smem = 0;
-        poly_body<KT, C, T, 2>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), pc,
-                            (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
+        WinCfg wc;
+        wc.chunk = im.chunk;
+        wc.band_h = im.band_h;
+        wc.waves = 0;
+        wc.swe = im.swe;
+        wc.raw_row = im.raw_row;
+        wc.band_cap = im.band_cap;
+        wc.pos_cap = im.pos_cap;
+        wc.tab_off = im.tab_off;
+        wc.raw_off = im.raw_off;
+        wc.smem = 0;
+        win_body<KT, C, T>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), wc,
+                                  (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
         __syncthreads();   // the next item reuses shared memory
     }
 }
@@ -210,23 +210,24 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
         const int chunks[2] = {sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4};
         for (int ch : chunks) {
             if (!ch) continue;
-            PolyCfg pc{};
-            pc.chunk = ch;
-            // batch items always stage shifted blocks (one kernel per class)
-            if (!poly_config(g, x.method, dtype, x.src, pc, true) || pc.smem > 100 * 1024) continue;
+            WinCfg wc{};
+            wc.chunk = ch;
+            // the general window body (the batch has no exact-x2 form: one kernel per class)
+            if (!win_config(g, x.method, dtype, wc, false) || wc.smem > 100 * 1024) continue;
             im.kind = 1;
-            im.chunk = pc.chunk;
-            im.band_h = std::min(pc.band_cap, sh.band);
-            im.w_swe_max = pc.swe_max;
-            im.band_cap = pc.band_cap;
-            im.pos_cap = pc.pos_cap;
-            im.vec = pc.vec;
-            im.raw_row = pc.raw_row;
-            im.raw_off = pc.raw_off;
-            im.tiles_x = (int)(((int64_t)x.Wo * x.C + 1023) / 1024);
+            im.chunk = wc.chunk;
+            im.band_h = std::min(wc.band_cap, sh.band);
+            im.swe = wc.swe;
+            im.band_cap = wc.band_cap;
+            im.pos_cap = wc.pos_cap;
+            im.tab_off = wc.tab_off;
+            im.raw_row = wc.raw_row;
+            im.raw_off = wc.raw_off;
+            const int sp = kWinThreads * win_pixels(x.C, dtype, false);
+            im.tiles_x = (int)(((int64_t)x.Wo + sp - 1) / sp);
             items = (int64_t)im.tiles_x * ((x.Ho + im.band_h - 1) / im.band_h);
-            smem = pc.smem;
-            cls = (pc.smem <= kWindowSmallSmem ? 0 : 8) + (x.method == RS_BILINEAR ? 0 : 4) + (x.C - 1);
+            smem = wc.smem;
+            cls = (wc.smem <= kWindowSmallSmem ? 0 : 8) + (x.method == RS_BILINEAR ? 0 : 4) + (x.C - 1);
             return RS_OK;
         }
     }
@@ -290,17 +291,17 @@ static rs_status batch_shape(const rs_image_desc* d, int n, int dtype, const rs_
         return RS_OK;
     }
     if (o.impl == RS_IMPL_WINDOW) {
-        sh = BatchShape{false, o.tile_h, o.tile_w ? o.tile_w : kPolyMaxBand};
+        sh = BatchShape{false, o.tile_h, o.tile_w ? o.tile_w : kWinMaxBand};
         if (sh.chunk && (sh.chunk < 4 || sh.chunk > 32)) return RS_ERR_INVALID_ARG;
-        if (sh.band < 1 || sh.band > kPolyMaxBand) return RS_ERR_INVALID_ARG;
+        if (sh.band < 1 || sh.band > kWinMaxBand) return RS_ERR_INVALID_ARG;
         return RS_OK;
     }
     if (o.impl != RS_IMPL_AUTO) return RS_ERR_INVALID_ARG;
-    sh = BatchShape{false, 0, kPolyMaxBand};
+    sh = BatchShape{false, 0, kWinMaxBand};
     Tuned t;
     if (tuned && tune_lookup(batch_key(d, n, dtype, o), t)) {
         if (t.impl == RS_IMPL_TILED) sh = BatchShape{true, 0, 0};
-        else if (t.impl == RS_IMPL_WINDOW && t.tile_w >= 1 && t.tile_w <= kPolyMaxBand) sh = BatchShape{false, t.tile_h, t.tile_w};
+        else if (t.impl == RS_IMPL_WINDOW && t.tile_w >= 1 && t.tile_w <= kWinMaxBand) sh = BatchShape{false, t.tile_h, t.tile_w};
     }
     return RS_OK;
 }
@@ -414,7 +415,7 @@ static cudaError_t class_launches(const BatchLayout& L, int dtype, const rs_opti
         if (L.count[c] == 0 || L.total[c] == 0) continue;
         ClassLaunch& cl = out[nl++];
         cl.func = class_func(dtype, c);
-        const int threads = c == kTileClass ? L.threads : 256;
+        const int threads = c == kTileClass ? L.threads : kWinThreads;
         int per_sm = 0;
         cudaError_t e = prepare_kernel(cl.func, L.smem[c], threads, &per_sm);
         if (e != cudaSuccess) return e;

@@ -31,7 +31,7 @@ struct KernelChoice {
     TileCfg tile;
     StreamCfg stream;
     int gather_w, gather_rows;   // RS_IMPL_GATHER: strip width, rows per thread
-    PolyCfg window;              // RS_IMPL_WINDOW
+    WinCfg window;               // RS_IMPL_WINDOW
 };
 rs_status choose_kernel(const Geom& g, int method, int dtype, const void* src, const rs_options& o,
                         KernelChoice& k);

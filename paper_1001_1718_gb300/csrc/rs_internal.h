@@ -92,13 +92,19 @@ struct StreamCfg {
 };
 
 // Configuration of the register-window kernel (bilinear / bicubic): strips
-// of 1024 output elements, bands of band_h output rows (0 = from occupancy
-// and `waves`), source rows staged in chunks of `chunk` rows (double
-// buffered) of swe_max elements; vec = staging mode (1: aligned 16-byte
-// units, 2: shifted aligned blocks around rows of any alignment).
-struct PolyCfg {
-    int chunk, band_h, waves, swe_max, band_cap, pos_cap, vec;
-    int raw_row, raw_off;   // vector path: bytes per raw staged row, byte offset of the raw ring
+// of kWinThreads * P output pixels (P per thread, win_pixels), bands of
+// band_h output rows (0 = from occupancy and `waves`), source rows staged
+// in chunks of `chunk` rows (a multiple of the taps). The rest are
+// host-computed bounds every block checks its own strip and band against
+// before touching shared memory.
+struct WinCfg {
+    int chunk, band_h, waves;
+    int swe;         // floats per staged FP32 row
+    int raw_row;     // bytes per raw staged row
+    int band_cap;    // rows of the row-tap tables (band_h <= band_cap)
+    int pos_cap;     // source positions of a band
+    int tab_off;     // byte offset of the row-tap tables in shared memory
+    int raw_off;     // byte offset of the raw ring in shared memory
     size_t smem;
 };
 
@@ -128,9 +134,14 @@ bool stream_config(const Geom& g, int method, int dtype, const void* src, Stream
 StreamCfg stream_default(const Geom& g, int method, int dtype, const void* src);
 cudaError_t launch_stream(const Geom& g, int method, int dtype, const void* src, void* dst, StreamCfg c,
                           cudaStream_t st);
-bool poly_config(const Geom& g, int method, int dtype, const void* src, PolyCfg& c, bool shifted_only = false);
-cudaError_t launch_poly(const Geom& g, int method, int dtype, const void* src, void* dst, PolyCfg c,
-                        cudaStream_t st);
+// Register-window kernel: pixels per thread, whether the exact-x2 form
+// applies (asymmetric map, both axes exactly doubled), configuration (false
+// if malformed or beyond shared memory; allow_x2 = false sizes the general
+// form even where the exact-x2 one applies) and launch.
+int win_pixels(int C, int dtype, bool x2);
+bool win_is_x2(const Geom& g);
+bool win_config(const Geom& g, int method, int dtype, WinCfg& c, bool allow_x2 = true);
+cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, void* dst, WinCfg c, cudaStream_t st);
 bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread);
 int nearest_default_rows(const Geom& g, int dtype);
 cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst, int tile_w, int rows_per_thread,
