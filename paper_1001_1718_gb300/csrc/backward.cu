@@ -798,7 +798,7 @@ static cudaError_t launch_adj_window(const Geom& g, const BwdPlan& p, const floa
     if (e != cudaSuccess) return e;
     const int64_t strips = ((int64_t)g.W * g.C + 2 * c.nt - 1) / (2 * c.nt);
     const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
-    const int64_t bands = std::max<int64_t>(1, (2 * resident + strips * g.planes - 1) / (strips * g.planes));
+    const int64_t bands = std::max<int64_t>(1, 2 * resident / (strips * g.planes));   // no partial extra wave
     c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.H + bands - 1) / bands));
     dim3 grid((unsigned)strips, (unsigned)((g.H + c.band_h - 1) / c.band_h), (unsigned)g.planes);
     unsigned int* fw = fault_word();

@@ -559,7 +559,7 @@ static int choose_band(const Geom& g, const StreamCfg& c, int per_sm, int waves)
 {
     const int64_t strips = ((int64_t)g.Wo * g.C + c.tile_w - 1) / c.tile_w;
     const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
-    const int64_t want = std::max<int64_t>(1, (resident * waves + strips * g.planes - 1) / (strips * g.planes));
+    const int64_t want = std::max<int64_t>(1, resident * waves / (strips * g.planes));   // no partial extra wave
     const int64_t chunks = (g.Ho + c.chunk_h - 1) / c.chunk_h;
     const int64_t bands = std::min<int64_t>(want, chunks);
     const int64_t chunks_per_band = std::min<int64_t>((chunks + bands - 1) / bands, c.band_cap / c.chunk_h);

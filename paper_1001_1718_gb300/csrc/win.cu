@@ -158,7 +158,8 @@ cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, vo
     if (c.band_h <= 0) {
         const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
         const int waves = c.waves > 0 ? c.waves : 2;
-        const int64_t bands = std::max<int64_t>(1, (resident * waves + strips * g.planes - 1) / (strips * g.planes));
+        // at most `waves` blocks per resident slot: a partial extra wave would run alone
+        const int64_t bands = std::max<int64_t>(1, resident * waves / (strips * g.planes));
         c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.Ho + bands - 1) / bands));
     }
     if (x2 && c.band_h % 2) ++c.band_h;   // bands start on even rows (band_cap = min(256, Ho) is even here)

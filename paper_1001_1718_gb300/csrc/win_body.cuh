@@ -352,16 +352,52 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // raw slot -> channel-planar FP32 rows, one warp per row, one pixel per
-    // lane; out-of-image pixels read the edge pixel (always in the footprint)
+    // raw slot -> channel-planar FP32 rows, one warp per row. Groups of 4
+    // in-image pixels: one lane reads their C * sizeof(T) words (one funnel
+    // shift realigns them), widens them and writes 4 floats to each plane.
+    // The other pixels (edge pads, a partial last group) one per lane; an
+    // out-of-image pixel reads the edge pixel (always in the footprint).
+    const int xin_lo = max(0, -px_lo), xin_hi = min(npx, g.W - px_lo);   // in-image staged pixels
+    const int g_lo = (xin_lo + 3) >> 2, g_hi = max(g_lo, xin_hi >> 2);   // whole in-image groups
+    const int x_lo4 = min(4 * g_lo, npx), x_hi4 = max(4 * g_hi, x_lo4);
     auto convert = [&](int c) {
         const int r0 = r_first + c * R, nn = chunk_rows(c);
         const unsigned char* rbase = RAW + (size_t)(c & 1) * R * cfg.raw_row;
         for (int k = warp; k < nn; k += kWinWarps) {
             const int phase = (int)(reinterpret_cast<uintptr_t>(row_ptr(r0 + k)) & 15);
-            const T* rr = reinterpret_cast<const T*>(rbase + k * cfg.raw_row + phase);   // element e at rr[e]
+            const unsigned char* rrow = rbase + k * cfg.raw_row;
             float* dr = SR + k * cfg.swe;
-            for (int x = lane; x < npx; x += 32) {
+            constexpr int GW = C * ES;   // words of a group of 4 pixels
+            const uint32_t* W = reinterpret_cast<const uint32_t*>(rrow) + (phase >> 2);
+            const int sh = 8 * (phase & 3);
+            for (int q = g_lo + lane; q < g_hi; q += 32) {
+                uint32_t x[GW + 1], y[GW];
+                #pragma unroll
+                for (int t = 0; t < GW + 1; ++t) x[t] = (ES < 4 || t < GW) ? W[q * GW + t] : 0u;
+                #pragma unroll
+                for (int t = 0; t < GW; ++t) y[t] = ES == 4 ? x[t] : __funnelshift_r(x[t], x[t + 1], sh);
+                #pragma unroll
+                for (int ch = 0; ch < C; ++ch) {
+                    float f[4];
+                    #pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int e = i * C + ch;   // element of the group
+                        if constexpr (ES == 1)
+                            f[i] = __int_as_float(__byte_perm(y[e >> 2], 0x4B000000u, 0x7650 + (e & 3))) - 8388608.0f;
+                        else if constexpr (ES == 2) {
+                            const uint32_t h16 = (y[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                            if constexpr (std::is_same<T, __half>::value) f[i] = __half2float(__ushort_as_half((unsigned short)h16));
+                            else f[i] = __uint_as_float(h16 << 16);
+                        } else
+                            f[i] = __uint_as_float(y[e]);
+                    }
+                    *reinterpret_cast<float4*>(dr + ch * sw + 4 * q) = make_float4(f[0], f[1], f[2], f[3]);
+                }
+            }
+            const T* rr = reinterpret_cast<const T*>(rrow + phase);   // element e at rr[e]
+            const int nedge = x_lo4 + (npx - x_hi4);
+            for (int t = lane; t < nedge; t += 32) {
+                const int x = t < x_lo4 ? t : x_hi4 + (t - x_lo4);
                 const int xs = min(max(px_lo + x, 0), g.W - 1) - px_lo;
                 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) dr[ch * sw + x] = win_widen(rr[xs * C + ch]);
@@ -462,11 +498,20 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
                 int slot[KT];
                 #pragma unroll
                 for (int x = 0; x < KT; ++x) slot[x] = (u + x) % KT;
+                // the rows of this position, two at a time (independent FMA chains)
                 const int nb = NC[b - b_first];
-                for (int k = 0; k < nb; ++k) {
-                    float2 v[NP][C];
-                    blend(RW + (size_t)(i + k) * KT, slot, v);
-                    put(i + k, v);
+                int k = 0;
+                for (; k + 1 < nb; k += 2) {
+                    float2 v0[NP][C], v1[NP][C];
+                    blend(RW + (size_t)(i + k) * KT, slot, v0);
+                    blend(RW + (size_t)(i + k + 1) * KT, slot, v1);
+                    put(i + k, v0);
+                    put(i + k + 1, v1);
+                }
+                if (k < nb) {
+                    float2 v0[NP][C];
+                    blend(RW + (size_t)(i + k) * KT, slot, v0);
+                    put(i + k, v0);
                 }
                 i += nb;
                 ++b;
