@@ -40,13 +40,13 @@ struct BatchImage {
 };
 
 // Classes: 0..7 = window (KT 2 / 4) x (C 1..4) with a footprint of at most
-// kWindowSmallSmem bytes of shared memory (four blocks per SM), 8..15 the
+// kWindowSmallSmem bytes of shared memory (three blocks per SM), 8..15 the
 // same with larger footprints (up to ~100 KB, two blocks per SM), 16 =
 // tiled. Splitting by footprint keeps one large image from lowering the
 // occupancy of its whole class.
 static constexpr int kClasses = 17;
 static constexpr int kTileClass = 16;
-static constexpr size_t kWindowSmallSmem = 56 * 1024;
+static constexpr size_t kWindowSmallSmem = 72 * 1024;
 
 __device__ __forceinline__ int find_image(const int64_t* __restrict__ start, int n, int64_t t)
 {
@@ -207,13 +207,16 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
     im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
     im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
     if (x.method != RS_NEAREST && !sh.tiled) {
-        const int chunks[2] = {sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4};
-        for (int ch : chunks) {
+        // chunks of 8 rows, else 4, within the small-footprint budget; else
+        // the same within ~100 KB (the large-footprint classes)
+        const int chunks[4] = {sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4, sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4};
+        for (int t = 0; t < 4; ++t) {
+            const int ch = chunks[t];
             if (!ch) continue;
             WinCfg wc{};
             wc.chunk = ch;
             // the general window body (the batch has no exact-x2 form: one kernel per class)
-            if (!win_config(g, x.method, dtype, wc, false) || wc.smem > 100 * 1024) continue;
+            if (!win_config(g, x.method, dtype, wc, false) || wc.smem > (t < 2 ? kWindowSmallSmem : 100 * 1024)) continue;
             im.kind = 1;
             im.chunk = wc.chunk;
             im.band_h = std::min(wc.band_cap, sh.band);
