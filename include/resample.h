@@ -277,13 +277,17 @@ rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype,
  * routine is called.
  *   - n > RS_NOALLOC_MAX_IMAGES returns RS_ERR_WORKSPACE, before any work.
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current).
  *   - Every call shares the one array and overwrites it (nothing in it needs
  *     to start at zero: each call writes all it reads). Calls whose work
  *     overlaps on the GPU (for example on two streams at once) race on it;
  *     calls on one stream run in order and are safe.
- *   - The descriptors are copied from host memory on `stream` before the
- *     launch; src / dst stay owned by the caller as in rs_resize_batched.
+ *   - The descriptors are copied from host staging memory on `stream` before
+ *     the launch (the call returns once they are staged); src / dst stay
+ *     owned by the caller as in rs_resize_batched. While `stream` is being
+ *     captured the call returns RS_ERR_UNSUPPORTED and does nothing: the next
+ *     call refills the staging memory a captured copy would read. Replayable
+ *     batches are rs_batched_plan_*'s job.
  */
 #define RS_NOALLOC_MAX_IMAGES 4096
 rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs_dtype dtype,

@@ -2,8 +2,9 @@
 //
 // The paper's question (Sec. IV, V) is whether one tile shape suits every
 // GPU and every scale; its answer is that it does not always. Here every
-// problem class (GPU, dtype, method, channel layout, coordinate mode, scale
-// class per axis, output size class) gets its own kernel and shape, chosen
+// problem class (GPU model and CUDA runtime, SM count, dtype, method, channel
+// layout, coordinate mode, scale class per axis, output size class) gets its
+// own kernel and shape, chosen
 // by timing the candidates on the caller's buffers with CUDA events.
 #include <algorithm>
 #include <cmath>
@@ -33,10 +34,10 @@ static std::string tune_key(const Geom& g, int method, int dtype)
 {
     const double elems = (double)g.Ho * g.Wo * g.C * g.planes;
     char buf[160];
-    std::snprintf(buf, sizeof buf, "sms=%d;dt=%d;m=%d;C=%d;coord=%d;sy=%d;sx=%d;sz=%d", num_sms(), dtype,
+    std::snprintf(buf, sizeof buf, ";sms=%d;dt=%d;m=%d;C=%d;coord=%d;sy=%d;sx=%d;sz=%d", num_sms(), dtype,
                   method, g.C, g.coord, scale_class(g.H, g.Ho), scale_class(g.W, g.Wo),
                   (int)std::floor(std::log2(std::max(1.0, elems))));
-    return buf;
+    return "gpu=" + device_tag() + buf;
 }
 
 bool tune_lookup(const std::string& key, Tuned& t)

@@ -259,8 +259,9 @@ struct BatchLayout {
 
 // Fills imgs_out (n entries) and start_out (n + kClasses entries) grouped
 // by class, with no allocation (scratch arrays are caller-provided, n each).
-// Tuning-cache key of a batch: GPU (SM count), dtype, count, coordinate map
-// and a hash of every descriptor's sizes, channels, method and pitches.
+// Tuning-cache key of a batch: GPU (model, CUDA runtime, SM count), dtype,
+// count, coordinate map and a hash of every descriptor's sizes, channels,
+// method and pitches.
 static std::string batch_key(const rs_image_desc* d, int n, int dtype, const rs_options& o)
 {
     uint64_t h = 1469598103934665603ull;   // FNV-1a
@@ -275,9 +276,9 @@ static std::string batch_key(const rs_image_desc* d, int n, int dtype, const rs_
         mix(d[k].method); mix(d[k].src_pitch); mix(d[k].dst_pitch);
     }
     char buf[96];
-    std::snprintf(buf, sizeof buf, "sms=%d;batch;dt=%d;n=%d;coord=%d;h=%016llx", num_sms(), dtype, n, o.coord,
+    std::snprintf(buf, sizeof buf, ";sms=%d;batch;dt=%d;n=%d;coord=%d;h=%016llx", num_sms(), dtype, n, o.coord,
                   (unsigned long long)h);
-    return buf;
+    return "gpu=" + device_tag() + buf;
 }
 
 // Item shape from the options: RS_IMPL_TILED (or an explicit tile shape with
@@ -535,18 +536,27 @@ extern "C" rs_status rs_resize_batched_noalloc(const rs_image_desc* d, int n, rs
     rs_status s = batch_layout(d, n, dtype, o, false, g_noalloc_imgs, g_noalloc_start, g_noalloc_tmp, g_noalloc_cls,
                                g_noalloc_items, L);
     if (s != RS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The descriptors are copied from host staging arrays that the next call
+    // refills; a captured copy would replay whatever they hold by then.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (cap != cudaStreamCaptureStatusNone) return RS_ERR_UNSUPPORTED;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 0 || dev >= kNoAllocMaxDevices) return RS_ERR_UNSUPPORTED;
     if (!g_noalloc_dev[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_batch_scratch);
-        if (e != cudaSuccess) return cuda_status(e);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();   // leave no sticky error for a later, unrelated check
+            return cuda_status(e);
+        }
         g_noalloc_dev[dev] = p;
     }
     char* scratch = static_cast<char*>(g_noalloc_dev[dev]);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Pageable source: each copy returns once the host data has been staged,
     // so the staging arrays may be refilled by the next call.
     e = cudaMemcpyAsync(scratch, g_noalloc_imgs, sizeof(BatchImage) * (size_t)n, cudaMemcpyHostToDevice, st);

@@ -4,6 +4,7 @@
 // cudaGetSymbolAddress (with that device current) and passed to kernels.
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 
 #include "rs_internal.h"
@@ -17,6 +18,7 @@ static std::mutex g_mu;
 static unsigned int* g_fault_ptr[kMaxDevices];
 static size_t g_smem[kMaxDevices];
 static int g_sms[kMaxDevices];
+static std::string g_tag[kMaxDevices];
 
 static int current_device()
 {
@@ -98,6 +100,35 @@ int num_sms()
         g_sms[dev] = v;
     }
     return g_sms[dev];
+}
+
+// "<device name>/cc<major><minor>/cudart<version>" with spaces replaced, for
+// tuning-cache keys: a cache from another GPU model or CUDA runtime does not
+// match.
+const std::string& device_tag()
+{
+    static const std::string none = "nodevice";
+    const int dev = current_device();
+    if (dev < 0) return none;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_tag[dev].empty()) {
+        cudaDeviceProp prop;
+        int rt = 0;
+        std::string t;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+            t = prop.name;
+            t += "/cc" + std::to_string(prop.major) + std::to_string(prop.minor);
+        } else {
+            (void)cudaGetLastError();
+            t = "unknown";
+        }
+        if (cudaRuntimeGetVersion(&rt) == cudaSuccess) t += "/cudart" + std::to_string(rt);
+        else (void)cudaGetLastError();
+        for (char& ch : t)
+            if (ch == ' ' || ch == ';' || ch == '\t') ch = '_';
+        g_tag[dev] = t;
+    }
+    return g_tag[dev];
 }
 
 int method_taps(int method)

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace rs {
 
 enum { COORD_ASYMMETRIC = 0, COORD_HALF_PIXEL = 1, COORD_ALIGN_CORNERS = 2 };
@@ -114,6 +116,9 @@ size_t dtype_size(int dtype);
 // Maximum dynamic shared memory a block may use on this device.
 size_t max_smem_per_block();
 int num_sms();
+// GPU name, compute capability and CUDA runtime version of the current
+// device, as one token (tuning-cache keys).
+const std::string& device_tag();
 // Raises func's dynamic shared-memory limit to at least smem bytes and, if
 // per_sm is given, returns its resident blocks per SM at `threads` threads
 // and smem bytes; both driver queries are cached per device and kernel.
