@@ -1,21 +1,25 @@
 """Benchmark of the resampling hot path on GB300.
 
-One step = the RGB uint8 4096x4096 smooth-field workload resampled three
-ways, each through the C ABI with the tiled kernel:
-    bicubic x2   -> 8192 x 8192
-    bicubic x1.7 -> 6963 x 6963
-    nearest x2   -> 8192 x 8192
-value = output pixels per step (an RGB pixel counts once) / device time of
-the step, in Gpixels/s, whole job over all ranks. L2 is flushed (a 256 MB
-write) before every timed step, outside the step's events.
+One step = the batched, autotuned, reduced-precision form: 256 RGB uint8
+images, H and W uniform on 64..2048, one scale per image uniform on [0.5, 4),
+methods alternating bilinear / bicubic, resampled by the library's
+replayable batch plan (one persistent launch per class, recorded as one CUDA
+graph) with item shapes chosen by rs_autotune_batched before the timed
+region. value = output pixels per step (an RGB pixel counts once) / device
+time of the step, in Gpixels/s, whole job over all ranks. L2 is flushed (a
+256 MB write) before every timed step, outside the step's events; a step's
+inputs and outputs (6.6 GB) are far larger than L2 anyway.
 
-Extra configurations (measured in the same run, reported under "extras"):
-uint8 bilinear 512x512 x2; float 8192x8192 bicubic x2 stored as FP32 / FP16 /
-BF16; the plain one-thread-per-pixel kernel on the same problems; NCHW FP32
-forward + backward; the ragged 256-image batch.
+Beside it (same run, "extras"): the paper's plain one-thread-per-pixel kernel
+on FP32 copies of the same 256 images (the same accuracy: max / mean error
+against the FP64 oracle reported for both), the same batch as one launch per
+image, the RGB uint8 4096x4096 step (bicubic x2, bicubic x1.7, nearest x2)
+with its dominant kernel's roofline, the single-channel 8192x8192 field in
+FP32 / FP16 / BF16, the 512x512 uint8 bilinear x2 latency (direct and CUDA
+graph replay), NCHW FP32 forward / backward / antialiased downscale.
 
---impl reference times the FP64 CPU oracle on the same workload (bounded
-sample per step) on this host's cores.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+batch (bands of output rows of 16 of its images) on this host's cores.
 """
 from __future__ import annotations
 
@@ -36,7 +40,9 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "output Gpixels/s and % of HBM roofline, batched/low-precision vs plain FP32, at stated error"
-HEADLINE_OPS = (("bicubic_x2", "bicubic", 2.0), ("bicubic_x1.7", "bicubic", 1.7), ("nearest_x2", "nearest", 2.0))
+BATCH_WORKLOAD = ("batch256_rgb_u8: 256 RGB uint8 images, H, W ~ U{64..2048}, scale ~ U[0.5, 4), "
+                  "bilinear / bicubic alternating, smooth-field pixels (seed 4)")
+RGB_OPS = (("bicubic_x2", "bicubic", 2.0), ("bicubic_x1.7", "bicubic", 1.7), ("nearest_x2", "nearest", 2.0))
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {"window": "k_win", "stream": "k_stream", "tiled": "k_tiled", "gather": "k_nearest",
                 "plain": "k_plain"}
@@ -45,21 +51,24 @@ KERNEL_NAMES = {"window": "k_win", "stream": "k_stream", "tiled": "k_tiled", "ga
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true", help="tune tile shapes before timing")
+    ap.add_argument("--no-autotune", action="store_true", help="time the batch plan with the default item shape")
     ap.add_argument("--tile-sweep", action="store_true",
                     help="the paper's tiling experiment on this GPU: an 800x800 uint8 image, bilinear at scales "
                          "2..10, the paper's kernel (one thread per output pixel) over block shapes, against "
                          "AUTO; prints a markdown table and exits")
-    ap.add_argument("--ops-only", nargs="?", const="headline", default=None,
-                    choices=["headline", "nchw", "backward", "batch"],
-                    help="profiling driver: run warmup + steps of the three headline resizes (headline), "
-                         "of the NCHW FP32 forward or backward x2 / x0.5 (nchw, backward) or of the "
-                         "256-image batch plan (batch), and exit")
+    ap.add_argument("--ops-only", nargs="?", const="batch", default=None,
+                    choices=["batch", "rgb", "nchw", "backward", "float"],
+                    help="profiling driver: run warmup + steps untimed launches of the 256-image batch plan "
+                         "(batch, the default), of the three RGB 4096 resizes (rgb), of the NCHW FP32 forward "
+                         "or backward x2 / x0.5 (nchw, backward) or of the float 8192 bicubic x2 in FP32 / "
+                         "FP16 / BF16 (float), and exit")
+    ap.add_argument("--batch-images", type=int, default=256,
+                    help="profiling drivers only: the first N images of the batch (a smaller capture)")
     return ap.parse_args()
 
 
@@ -166,6 +175,7 @@ class ClockSampler:
 # Source files each profiled kernel is built from (a change to any of them
 # voids its recorded DRAM traffic).
 KERNEL_SOURCES = {
+    "k_batched_window": ["batched.cu", "win_body.cuh", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_win": ["win.cu", "win_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_stream": ["stream.cu", "rs_common.cuh", "rs_internal.h"],
     "k_tiled": ["tiled.cu", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
@@ -233,32 +243,48 @@ def time_ops(torch, stream, ops, steps, warmup, flush):
             for k, (name, _) in enumerate(ops)}
 
 
-def sample_errors(oracle, img64, outs, methods, seed=0, n=4096):
-    """max / mean |gpu - FP64 oracle| on n sampled output points per op."""
-    from paper_1001_1718_gb300 import workloads
-    res = {}
-    for name, (y, code) in outs.items():
-        Ho, Wo = y.shape[0], y.shape[1]
-        ys, xs = workloads.sample_points(seed, Ho, Wo, n)
-        ref = oracle.resize_points(img64, Ho, Wo, code, 0, -0.5, ys, xs)
-        got = y[torch_index(ys), torch_index(xs)].cpu().numpy().astype(np.float64)
-        q = oracle.quantize_u8(ref).astype(np.float64)
-        res[name] = {"max_abs_vs_f64": float(np.abs(got - ref).max()),
-                     "mean_abs_vs_f64": float(np.abs(got - ref).mean()),
-                     "max_steps_vs_rounded_oracle": float(np.abs(got - q).max()),
-                     "points": int(n)}
-    return res
-
-
 def torch_index(a):
     import torch
     return torch.from_numpy(np.asarray(a, np.int64)).cuda()
 
 
+class Batch:
+    """The 256-image ragged batch: host pixels, device inputs and outputs."""
+
+    def __init__(self, torch, workloads, dev, n=256):
+        self.items = workloads.batch_spec(seed=4)[:n]
+        self.imgs = workloads.batch_images(self.items)
+        self.srcs = [torch.from_numpy(im).to(dev) for im in self.imgs]
+        self.outs = [torch.empty((it.Ho, it.Wo, 3), dtype=torch.uint8, device=dev) for it in self.items]
+        self.methods = [workloads.METHOD_NAMES[it.method] for it in self.items]
+        self.in_bytes = sum(x.numel() for x in self.srcs)
+        self.out_bytes = sum(y.numel() for y in self.outs)
+        self.out_px = sum(it.Ho * it.Wo for it in self.items)
+
+
+def batch_errors(oracle, batch, outs, dtype="u8", n=512, every=16):
+    """max / mean |gpu - FP64 oracle| (and uint8 steps off the rounded
+    oracle) on n sampled points of every `every`-th image."""
+    from paper_1001_1718_gb300 import workloads
+    err, steps, tot, cnt = 0.0, 0.0, 0.0, 0
+    for k in range(0, len(batch.items), every):
+        it = batch.items[k]
+        ys, xs = workloads.sample_points(k, it.Ho, it.Wo, n)
+        ref = oracle.resize_points(batch.imgs[k].astype(np.float64), it.Ho, it.Wo, it.method, 0, -0.5, ys, xs)
+        got = outs[k][torch_index(ys), torch_index(xs)].double().cpu().numpy()
+        d = np.abs(got - ref)
+        err, tot, cnt = max(err, float(d.max())), tot + float(d.sum()), cnt + d.size
+        if dtype == "u8":
+            steps = max(steps, float(np.abs(got - oracle.quantize_u8(ref)).max()))
+    r = {"max_abs_vs_f64": err, "mean_abs_vs_f64": tot / max(1, cnt),
+         "points": cnt, "images": len(range(0, len(batch.items), every))}
+    if dtype == "u8":
+        r["max_steps_vs_rounded_oracle"] = steps
+    return r
+
+
 def profile_ops(args, torch, rs, workloads, dev):
-    """Untimed launches for profiling under ncu: the NCHW FP32 forward or
-    backward (bilinear / bicubic, x2 and x0.5 of 32x3x512x512) or the
-    replayable plan of the 256-image ragged batch."""
+    """Untimed launches for profiling under ncu."""
     if args.ops_only == "nchw":
         xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
         ops = []
@@ -278,11 +304,24 @@ def profile_ops(args, torch, rs, workloads, dev):
                 ws = torch.empty(rs.backward_workspace_bytes(g, (512, 512), method), dtype=torch.uint8, device=dev)
                 ops.append(lambda g=g, gi=gi, ws=ws, m=method: rs.resize_backward(g, (512, 512), m, grad_in=gi,
                                                                                  workspace=ws))
+    elif args.ops_only == "rgb":
+        img = workloads.workload_rgb_4096(seed=2)
+        x = torch.from_numpy(img).to(dev)
+        ops = []
+        for _, method, s in RGB_OPS:
+            Ho = out_hw(4096, s)
+            y = torch.empty((Ho, Ho, 3), dtype=torch.uint8, device=dev)
+            ops.append(lambda y=y, m=method, Ho=Ho: rs.resize(x, (Ho, Ho), m, out=y))
+    elif args.ops_only == "float":
+        f64 = workloads.workload_float_8192(seed=3)
+        ops = []
+        for tdt in (torch.float32, torch.float16, torch.bfloat16):
+            xf = torch.from_numpy(f64).to(dev).to(tdt)
+            yf = torch.empty((16384, 16384), dtype=tdt, device=dev)
+            ops.append(lambda xf=xf, yf=yf: rs.resize(xf, (16384, 16384), "bicubic", out=yf))
     else:
-        items = workloads.batch_spec(seed=4)
-        srcs = [torch.from_numpy(im).to(dev) for im in workloads.batch_images(items)]
-        outs = [torch.empty((it.Ho, it.Wo, 3), dtype=torch.uint8, device=dev) for it in items]
-        plan = rs.BatchedPlan(srcs, outs, [workloads.METHOD_NAMES[it.method] for it in items])
+        b = Batch(torch, workloads, dev, args.batch_images)
+        plan = rs.BatchedPlan(b.srcs, b.outs, b.methods)
         ops = [plan.launch]
     for _ in range(args.warmup + args.steps):
         for fn in ops:
@@ -300,188 +339,163 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream(dev)
 
-    if args.ops_only in ("nchw", "backward", "batch"):
+    if args.ops_only:
         profile_ops(args, torch, rs, workloads, dev)
         return None
 
-    img = workloads.workload_rgb_4096(seed=2)
-    H, W, C = img.shape
-    x = torch.from_numpy(img).to(dev)
-    outs = {}
-    ops = []
-    for name, method, s in HEADLINE_OPS:
-        Ho, Wo = out_hw(H, s), out_hw(W, s)
-        y = torch.empty((Ho, Wo, C), dtype=torch.uint8, device=dev)
-        outs[name] = (y, rs.METHODS[method])
-        if args.autotune:
-            rs.autotune(x, (Ho, Wo), method, out=y)
-        ops.append((name, (lambda y=y, m=method, Ho=Ho, Wo=Wo: rs.resize(x, (Ho, Wo), m, out=y))))
-    px_per_step = sum(y.shape[0] * y.shape[1] for y, _ in outs.values())
-    if args.ops_only:
-        for _ in range(args.warmup + args.steps):
-            for _, fn in ops:
-                fn()
-        torch.cuda.synchronize()
-        return None
+    b = Batch(torch, workloads, dev)
+    tuned = None
+    if not args.no_autotune:   # outside the timed region; cached for the plan below
+        tuned = rs.autotune_batched(b.srcs, b.outs, b.methods)
+    plan = rs.BatchedPlan(b.srcs, b.outs, b.methods)
+    kernels = plan.kernels()
     flush = Flusher(torch, dev)
 
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    times = time_ops(torch, stream, ops, args.steps, args.warmup, flush)
+    times = time_ops(torch, stream, [("batch", plan.launch)], args.steps, args.warmup, flush)["batch"]
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
 
-    step_ms = [sum(times[n][s] for n, _ in ops) for s in range(args.steps)]
-    px_per_s, total_s = aggregate(px_per_step, args.steps, sum(step_ms) / 1e3, world)
+    px_per_s, total_s = aggregate(b.out_px, args.steps, sum(times) / 1e3, world)
     value = px_per_s / 1e9
     assert rs.debug_fault() == 0, "a kernel reported a bound violation"
 
-    # Roofline of the dominant kernel (bicubic x2): algorithmic bytes = source
-    # read once + output written once.
-    bc_ms = statistics.mean(times["bicubic_x2"])
-    Ho2, Wo2 = outs["bicubic_x2"][0].shape[:2]
-    alg_bytes = H * W * C + Ho2 * Wo2 * C
-    achieved = alg_bytes / (bc_ms / 1e3) / 1e9
-    chosen = rs.tile_config(x, (Ho2, Wo2), "bicubic")
-    kname = KERNEL_NAMES.get(chosen["impl"], chosen["impl"])
-    traffic = traffic_from_profile(kname, "rgb4096_bicubic_x2")
-    per_op = {n: {"ms": statistics.mean(times[n]),
-                  "gpx_s": outs[n][0].shape[0] * outs[n][0].shape[1] / (statistics.mean(times[n]) / 1e3) / 1e9,
-                  "hbm_gbs": (H * W * C + outs[n][0].numel()) / (statistics.mean(times[n]) / 1e3) / 1e9}
-              for n, _ in ops}
-    for n in per_op:
-        per_op[n]["frac_of_hbm_peak"] = per_op[n]["hbm_gbs"] / hbm_peak
+    # Roofline of the step's one launch (the plan): algorithmic bytes = every
+    # source read once + every output written once.
+    mean_ms = statistics.mean(times)
+    alg_bytes = b.in_bytes + b.out_bytes
+    achieved = alg_bytes / (mean_ms / 1e3) / 1e9
+    traffic = traffic_from_profile("k_batched_window", "batch256")
 
-    # End to end through the public API with host buffers: H2D of the input
-    # from pinned memory, the three resizes, D2H of the three outputs.
-    e2e = run_e2e(torch, rs, img, outs, dev, stream, min(args.steps, 20), 3)
+    e2e = run_e2e_batch(torch, b, plan, dev, stream, min(args.steps, 10), 2)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "rgb_u8_4096x4096_smooth_field: bicubic x2, bicubic x1.7, nearest x2",
-                   "storage": "u8 HWC interleaved, C=3", "coord": "asymmetric (Eq. 1)", "cubic_a": -0.5,
-                   "kernel": "library default per op (rs_resize_ex, RS_IMPL_AUTO)",
-                   "l2": "flushed before every timed step (256 MB write)",
-                   "parallelism": f"replicas x{world} (independent images per GPU)",
-                   "output_px_per_step": px_per_step},
+        "config": {"workload": BATCH_WORKLOAD, "images": len(b.items), "storage": "u8 HWC interleaved, C=3",
+                   "coord": "asymmetric (Eq. 1)", "cubic_a": -0.5,
+                   "kernel": f"replayable batch plan: {kernels} persistent class launches in one CUDA graph",
+                   "item_shape": ({"autotuned": True, **tuned} if tuned else {"autotuned": False}),
+                   "l2": "flushed before every timed step (256 MB write); step I/O 6.6 GB",
+                   "parallelism": f"replicas x{world} (each GPU its own batch)",
+                   "output_px_per_step": b.out_px, "in_bytes_per_step": b.in_bytes,
+                   "out_bytes_per_step": b.out_bytes},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": f"{kname}<bicubic, C=3, u8> bicubic x2 ({chosen})",
+                     "kernel": f"the batch plan ({kernels} k_batched_window / k_batched class launches, one graph)",
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": f"{peak_kind} copy bandwidth"},
-        "per_op": per_op,
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": len(ops) * args.steps,
+        "gpu_launches": kernels * args.steps,
     }
     if rank == 0:
         from oracle import oracle
         oracle.build()
-        line["error"] = sample_errors(oracle, img.astype(np.float64), outs, None)
+        line["error"] = batch_errors(oracle, b, b.outs)
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(oracle, img, budget_s=8.0)
+            line["cpu_baseline"] = cpu_baseline(oracle, b, budget_s=8.0)
         if not args.no_extras:
-            line["extras"] = extras(torch, rs, dev, stream, oracle, hbm_peak)
+            line["extras"] = extras(torch, rs, dev, stream, oracle, hbm_peak, b)
+    plan.close()
     return line
 
 
-def run_e2e(torch, rs, img, outs, dev, stream, steps, warmup):
-    host_in = torch.from_numpy(img).pin_memory()
-    host_out = {n: torch.empty(y.shape, dtype=y.dtype).pin_memory() for n, (y, _) in outs.items()}
-    dev_in = torch.empty(img.shape, dtype=torch.uint8, device=dev)
-    names = [n for n, _, _ in HEADLINE_OPS]
-    meth = {n: m for n, m, _ in HEADLINE_OPS}
-
-    # Each output's device-to-host copy runs on a copy stream as soon as its
-    # resize is done, overlapping the next resizes and the next step's
-    # host-to-device copy; a resize waits until the previous copy of its
-    # output buffer has finished.
+def run_e2e_batch(torch, b, plan, dev, stream, steps, warmup):
+    """The batch end to end through the public API with host buffers: every
+    step copies the 256 inputs from pinned host memory, replays the plan and
+    copies the 256 outputs back to pinned host memory. A step's outputs go
+    back on a copy stream while the next step's inputs come in; the next
+    replay waits until the previous outputs have been read."""
+    host_in = [torch.from_numpy(im).pin_memory() for im in b.imgs]
+    host_out = [torch.empty(y.shape, dtype=y.dtype, pin_memory=True) for y in b.outs]
     copy_stream = torch.cuda.Stream(dev)
-    ev_k = {n: torch.cuda.Event() for n in names}
-    ev_c = {n: torch.cuda.Event() for n in names}
-    for n in names:
-        ev_c[n].record(copy_stream)
+    ev_plan, ev_out = torch.cuda.Event(), torch.cuda.Event()
+    ev_out.record(copy_stream)
 
     def step():
-        dev_in.copy_(host_in, non_blocking=True)
-        for n in names:
-            y = outs[n][0]
-            stream.wait_event(ev_c[n])
-            rs.resize(dev_in, y.shape[:2], meth[n], out=y)
-            ev_k[n].record(stream)
-            copy_stream.wait_event(ev_k[n])
-            with torch.cuda.stream(copy_stream):
-                host_out[n].copy_(y, non_blocking=True)
-            ev_c[n].record(copy_stream)
+        with torch.cuda.stream(stream):
+            for h, d in zip(host_in, b.srcs):
+                d.copy_(h, non_blocking=True)
+            stream.wait_event(ev_out)
+            plan.launch()
+            ev_plan.record(stream)
+        copy_stream.wait_event(ev_plan)
+        with torch.cuda.stream(copy_stream):
+            for d, h in zip(b.outs, host_out):
+                h.copy_(d, non_blocking=True)
+            ev_out.record(copy_stream)
 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(steps):
         step()
-    for n in names:   # the timed region ends when every copy has landed
-        stream.wait_event(ev_c[n])
-    b.record(stream)
+    stream.wait_event(ev_out)   # the timed region ends when every output has landed
+    e.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
-    px = sum(outs[n][0].shape[0] * outs[n][0].shape[1] for n in names)
-    return {"value": px / (ms / 1e3) / 1e9, "unit": "Gpixels/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": int(host_in.numel()),
-            "d2h_bytes_per_step": int(sum(t.numel() for t in host_out.values()))}
+    ms = a.elapsed_time(e) / steps
+    return {"value": b.out_px / (ms / 1e3) / 1e9, "unit": "Gpixels/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(b.in_bytes), "d2h_bytes_per_step": int(b.out_bytes),
+            "note": "pinned host buffers; bound by the device-to-host link"}
 
 
-def cpu_baseline(oracle, img, budget_s=8.0, band=64, single_s=2.0):
-    """The FP64 oracle on this host's cores on a bounded sample of the step:
-    bands of `band` output rows of each of the three outputs, round robin,
-    until `budget_s` seconds of wall time have been spent; then the same on
-    one thread for `single_s` seconds (reported beside it)."""
-    line = _oracle_sample(oracle, img, budget_s, band)
+def _oracle_batch_sample(oracle, b, budget_s, band=16, every=16, max_steps=None):
+    """The FP64 oracle on bands of `band` output rows of every `every`-th
+    batch image, round robin, until `budget_s` seconds of wall time (or
+    max_steps bands) have been spent."""
+    picks = list(range(0, len(b.items), every))
+    if not hasattr(b, "f64"):
+        b.f64 = {}   # FP64 copies of the sampled images, made once
+    f64 = b.f64
+    px, k = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and (max_steps is None or k < max_steps):
+        idx = picks[k % len(picks)]
+        it = b.items[idx]
+        if idx not in f64:
+            f64[idx] = b.imgs[idx].astype(np.float64)
+        nb = min(band, it.Ho)
+        y0 = (k * 131) % max(1, it.Ho - nb + 1)
+        ys = np.repeat(np.arange(y0, y0 + nb), it.Wo)
+        xs = np.tile(np.arange(it.Wo), nb)
+        oracle.resize_points(f64[idx], it.Ho, it.Wo, it.method, 0, -0.5, ys, xs)
+        px += len(ys)
+        k += 1
+    dt = time.perf_counter() - t0
+    return px, dt, k, len(picks)
+
+
+def cpu_baseline(oracle, b, budget_s=8.0, single_s=2.0):
+    """The FP64 oracle on this host's cores on a bounded sample of the batch
+    step (bands of output rows of 16 of its images), then the same on one
+    thread (reported beside it)."""
+    px, dt, k, npk = _oracle_batch_sample(oracle, b, budget_s)
+    line = {"value": px / dt / 1e9, "unit": "Gpixels/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{k} bands of 16 output rows round robin over {npk} of the 256 batch images "
+                      f"({px} output px, {dt:.1f} s wall)"}
     if single_s > 0:
         cores = oracle.num_threads()
         oracle.set_num_threads(1)
         try:
-            one = _oracle_sample(oracle, img, single_s, band)
+            px1, dt1, k1, _ = _oracle_batch_sample(oracle, b, single_s)
         finally:
             oracle.set_num_threads(cores)
-        line["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": 1, "sample": one["sample"]}
+        line["single_thread"] = {"value": px1 / dt1 / 1e9, "unit": "Gpixels/s", "cores": 1,
+                                 "sample": f"{k1} bands ({px1} output px, {dt1:.1f} s wall)"}
     return line
-
-
-def _oracle_sample(oracle, img, budget_s, band):
-    x = img.astype(np.float64)
-    H, W, C = img.shape
-    jobs = []
-    for name, method, s in HEADLINE_OPS:
-        Ho, Wo = out_hw(H, s), out_hw(W, s)
-        code = {"nearest": 0, "bilinear": 1, "bicubic": 2}[method]
-        jobs.append((Ho, Wo, code))
-    px = 0
-    t0 = time.perf_counter()
-    k = 0
-    while time.perf_counter() - t0 < budget_s:
-        Ho, Wo, code = jobs[k % 3]
-        y0 = (k * 997 * band) % max(1, Ho - band)
-        ys = np.repeat(np.arange(y0, y0 + band), Wo)
-        xs = np.tile(np.arange(Wo), band)
-        oracle.resize_points(x, Ho, Wo, code, 0, -0.5, ys, xs)
-        px += len(ys)
-        k += 1
-    dt = time.perf_counter() - t0
-    return {"value": px / dt / 1e9, "unit": "Gpixels/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{k} bands of {band} output rows round robin over bicubic x2 / bicubic x1.7 / nearest x2 "
-                      f"({px} output px, {dt:.1f} s wall)"}
 
 
 # --------------------------------------------------------------------------
 # Extra configurations
 
-def extras(torch, rs, dev, stream, oracle, hbm_peak):
+def extras(torch, rs, dev, stream, oracle, hbm_peak, b):
     from paper_1001_1718_gb300 import workloads
     ex = {}
     flush = Flusher(torch, dev)
@@ -494,33 +508,86 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak):
         gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
         ex[name] = {"ms": ms, "gpx_s": out_px / (ms / 1e3) / 1e9, "hbm_gbs": gbs,
                     "frac_of_hbm_peak": gbs / hbm_peak, **kw}
+        return ex[name]
 
-    # uint8 512x512 bilinear x2 (L2-resident, launch-bound)
-    img1, (Ho, Wo) = workloads.workload_u8_bilinear_512(seed=1)
-    x1 = torch.from_numpy(img1).to(dev)
-    y1 = torch.empty((Ho, Wo, 1), dtype=torch.uint8, device=dev)
-    for impl in ("auto", "plain"):
-        ms = bench(lambda: rs.resize(x1, (Ho, Wo), "bilinear", out=y1, impl=impl), 50)
-        ref = oracle.quantize_u8(oracle.resize(img1.astype(np.float64), Ho, Wo, 1))
-        exact = bool(np.array_equal(y1.cpu().numpy(), ref))
-        rec(f"u8_512_bilinear_x2_{impl}", ms, img1.size, y1.numel(), Ho * Wo, bit_exact_vs_oracle=exact,
-            note="L2-resident: roofline fraction not meaningful")
+    # --- the batch beside it: one launch per image (AUTO), and the paper's
+    # plain kernel (one thread per output pixel, 32x4 blocks) on FP32 copies
+    def per_image():
+        for x, y, m in zip(b.srcs, b.outs, b.methods):
+            rs.resize(x, y.shape[:2], m, out=y)
+    ms = bench(per_image, 5)
+    rec("batch256_u8_one_launch_per_image", ms, b.in_bytes, b.out_bytes, b.out_px, launches=len(b.items))
+    x32 = [x.float() for x in b.srcs]
+    y32 = [torch.empty(y.shape, dtype=torch.float32, device=dev) for y in b.outs]
 
-    # float 8192x8192 bicubic x2 stored as FP32 / FP16 / BF16
+    def plain_all():
+        for x, y, m in zip(x32, y32, b.methods):
+            rs.resize(x, y.shape[:2], m, out=y, impl="plain")
+    ms = bench(plain_all, 3)
+    rec("batch256_f32_plain_kernel", ms, 4 * b.in_bytes, 4 * b.out_bytes, b.out_px, launches=len(b.items),
+        note="the paper's kernel (Sec. III.A, Eq. 6; 32x4 blocks) on FP32 copies of the batch",
+        error=batch_errors(oracle, b, y32, "f32"))
+    del x32, y32
+    torch.cuda.empty_cache()
+
+    # --- RGB uint8 4096x4096: bicubic x2, bicubic x1.7, nearest x2 (AUTO),
+    # with the roofline of its dominant launch (the exact-x2 window kernel)
+    img = workloads.workload_rgb_4096(seed=2)
+    x = torch.from_numpy(img).to(dev)
+    outs = {}
+    ops = []
+    for name, method, s in RGB_OPS:
+        Ho = out_hw(4096, s)
+        y = torch.empty((Ho, Ho, 3), dtype=torch.uint8, device=dev)
+        outs[name] = (y, rs.METHODS[method])
+        ops.append((name, (lambda y=y, m=method, Ho=Ho: rs.resize(x, (Ho, Ho), m, out=y))))
+    times = time_ops(torch, stream, ops, 50, 5, flush)
+    step_ms = [sum(times[n][k] for n, _ in ops) for k in range(50)]
+    px = sum(y.shape[0] * y.shape[1] for y, _ in outs.values())
+    per_op = {}
+    for n, _ in ops:
+        ms = statistics.mean(times[n])
+        byt = img.size + outs[n][0].numel()
+        per_op[n] = {"ms": ms, "gpx_s": outs[n][0].shape[0] * outs[n][0].shape[1] / (ms / 1e3) / 1e9,
+                     "hbm_gbs": byt / (ms / 1e3) / 1e9, "frac_of_hbm_peak": byt / (ms / 1e3) / 1e9 / hbm_peak}
+    chosen = rs.tile_config(x, (8192, 8192), "bicubic")
+    kname = KERNEL_NAMES.get(chosen["impl"], chosen["impl"])
+    errs = {}
+    x64 = img.astype(np.float64)
+    for n, (y, code) in outs.items():
+        ys, xs = workloads.sample_points(7, y.shape[0], y.shape[1], 4096)
+        ref = oracle.resize_points(x64, y.shape[0], y.shape[1], code, 0, -0.5, ys, xs)
+        got = y[torch_index(ys), torch_index(xs)].cpu().numpy().astype(np.float64)
+        errs[n] = {"max_abs_vs_f64": float(np.abs(got - ref).max()), "mean_abs_vs_f64": float(np.abs(got - ref).mean()),
+                   "max_steps_vs_rounded_oracle": float(np.abs(got - oracle.quantize_u8(ref)).max())}
+    bc = per_op["bicubic_x2"]
+    ex["rgb4096_u8_step"] = {
+        "ms": statistics.mean(step_ms), "gpx_s": px / (statistics.mean(step_ms) / 1e3) / 1e9, "per_op": per_op,
+        "error_sampled_4096_points": errs,
+        "roofline": {"bound": "hbm", "achieved": bc["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                     "frac": bc["frac_of_hbm_peak"], "traffic": traffic_from_profile(kname, "rgb4096_bicubic_x2"),
+                     "kernel": f"{kname}<bicubic, C=3, u8> exact x2 ({chosen})",
+                     "algorithmic_bytes_per_launch": img.size + 8192 * 8192 * 3}}
+    ms = bench(lambda: rs.resize(x, (8192, 8192), "bicubic", out=outs["bicubic_x2"][0], impl="plain"), 10)
+    rec("rgb4096_u8_bicubic_x2_plain_kernel", ms, img.size, 8192 * 8192 * 3, 8192 * 8192)
+    del x, outs, ops
+    torch.cuda.empty_cache()
+
+    # --- single-channel 8192x8192 field, bicubic x2, stored as FP32 / FP16 / BF16
     f64 = workloads.workload_float_8192(seed=3)
     Hf, Wf = f64.shape
     ys, xs = workloads.sample_points(3, 2 * Hf, 2 * Wf, 2048)
+    ref_true = oracle.resize_points(f64, 2 * Hf, 2 * Wf, 2, 0, -0.5, ys, xs)[:, 0]
     for dt_name, tdt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
         xf = torch.from_numpy(f64).to(dev).to(tdt)
         yf = torch.empty((2 * Hf, 2 * Wf), dtype=tdt, device=dev)
         stored64 = xf.to(torch.float64).cpu().numpy()
         ref = oracle.resize_points(stored64, 2 * Hf, 2 * Wf, 2, 0, -0.5, ys, xs)[:, 0]
-        ref_true = oracle.resize_points(f64, 2 * Hf, 2 * Wf, 2, 0, -0.5, ys, xs)[:, 0]
         for impl in (("auto", "plain") if dt_name == "f32" else ("auto",)):
             ms = bench(lambda: rs.resize(xf, (2 * Hf, 2 * Wf), "bicubic", out=yf, impl=impl), 10)
             got = yf[torch_index(ys), torch_index(xs)].to(torch.float64).cpu().numpy()
             es = xf.element_size()
-            rec(f"float_8192_bicubic_x2_{dt_name}_{impl}", ms, Hf * Wf * es, 4 * Hf * Wf * es, 4 * Hf * Wf,
+            rec(f"float8192_bicubic_x2_{dt_name}_{impl}", ms, Hf * Wf * es, 4 * Hf * Wf * es, 4 * Hf * Wf,
                 max_abs_vs_f64_of_stored_input=float(np.abs(got - ref).max()),
                 mean_abs_vs_f64_of_stored_input=float(np.abs(got - ref).mean()),
                 max_abs_vs_f64_of_fp64_input=float(np.abs(got - ref_true).max()),
@@ -528,39 +595,42 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak):
         del xf, yf
     torch.cuda.empty_cache()
 
-    # ragged batch: one persistent launch replayed from a CUDA graph, vs
-    # one launch per image
-    items = workloads.batch_spec(seed=4)
-    imgs = workloads.batch_images(items)
-    srcs = [torch.from_numpy(im).to(dev) for im in imgs]
-    outs = [torch.empty((it.Ho, it.Wo, 3), dtype=torch.uint8, device=dev) for it in items]
-    meths = [workloads.METHOD_NAMES[it.method] for it in items]
-    in_b = sum(x.numel() for x in srcs)
-    out_b = sum(y.numel() for y in outs)
-    out_px = sum(it.Ho * it.Wo for it in items)
-    plan = rs.BatchedPlan(srcs, outs, meths)
-    ms = bench(lambda: plan.launch(), 10)
-    ys, xs = workloads.sample_points(4, items[0].Ho, items[0].Wo, 512)
-    errs = []
-    for k in (0, 1, 100, 255):
-        it = items[k]
-        ys, xs = workloads.sample_points(k, it.Ho, it.Wo, 512)
-        ref = oracle.resize_points(imgs[k].astype(np.float64), it.Ho, it.Wo, it.method, 0, -0.5, ys, xs)
-        got = outs[k][torch_index(ys), torch_index(xs)].cpu().numpy().astype(np.float64)
-        errs.append(float(np.abs(got - oracle.quantize_u8(ref)).max()))
-    rec("batch256_rgb_u8_graph", ms, in_b, out_b, out_px, images=len(items),
-        max_steps_vs_rounded_oracle_sampled=max(errs), launches=1)
+    # --- uint8 512x512 bilinear x2 (L2-resident, launch-bound): device time
+    # of a direct launch, and of one replay of a CUDA graph holding the call
+    img1, (Ho, Wo) = workloads.workload_u8_bilinear_512(seed=1)
+    x1 = torch.from_numpy(img1).to(dev)
+    y1 = torch.empty((Ho, Wo, 1), dtype=torch.uint8, device=dev)
+    ref1 = oracle.quantize_u8(oracle.resize(img1.astype(np.float64), Ho, Wo, 1))
+    for impl in ("auto", "plain"):
+        ms = bench(lambda: rs.resize(x1, (Ho, Wo), "bilinear", out=y1, impl=impl), 50)
+        rec(f"u8_512_bilinear_x2_{impl}", ms, img1.size, y1.numel(), Ho * Wo,
+            bit_exact_vs_oracle=bool(np.array_equal(y1.cpu().numpy(), ref1)),
+            note="L2-resident: roofline fraction not meaningful")
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        rs.resize(x1, (Ho, Wo), "bilinear", out=y1)   # warm the library's per-kernel caches
+    side.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        rs.resize(x1, (Ho, Wo), "bilinear", out=y1)
+    y1.zero_()
+    ms = bench(graph.replay, 50)
+    reps = 200
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e.record(stream)
+    torch.cuda.synchronize()
+    rec("u8_512_bilinear_x2_graph_replay", ms, img1.size, y1.numel(), Ho * Wo,
+        back_to_back_us_per_replay=a.elapsed_time(e) * 1e3 / reps,
+        bit_exact_vs_oracle=bool(np.array_equal(y1.cpu().numpy(), ref1)),
+        note="one replay of a CUDA graph holding the resize (device time, L2 flushed before)")
+    del graph
 
-    def per_image():
-        for x, y, m in zip(srcs, outs, meths):
-            rs.resize(x, y.shape[:2], m, out=y)
-    ms = bench(per_image, 5)
-    rec("batch256_rgb_u8_per_image_launches", ms, in_b, out_b, out_px, images=len(items), launches=len(items))
-    plan.close()
-    del srcs, outs, plan
-    torch.cuda.empty_cache()
-
-    # NCHW FP32 32x3x512x512: forward and backward, x2 and x0.5
+    # --- NCHW FP32 32x3x512x512: forward and backward, x2 and x0.5
     xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
     for method in ("bilinear", "bicubic"):
         for s in (2.0, 0.5):
@@ -585,20 +655,21 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak):
             del y, g, gi, ws
     del xn
     torch.cuda.empty_cache()
-
-    # plain kernel on the headline's dominant problem
-    img = workloads.workload_rgb_4096(seed=2)
-    x = torch.from_numpy(img).to(dev)
-    y = torch.empty((8192, 8192, 3), dtype=torch.uint8, device=dev)
-    ms = bench(lambda: rs.resize(x, (8192, 8192), "bicubic", out=y, impl="plain"), 10)
-    rec("rgb_u8_4096_bicubic_x2_plain", ms, img.size, y.numel(), 8192 * 8192)
-    del x, y
-    torch.cuda.empty_cache()
     return ex
 
 
 # --------------------------------------------------------------------------
 # Reference arm: the FP64 CPU oracle on this host's cores
+
+class _HostBatch:
+    """The batch's host side only (no device)."""
+
+    def __init__(self, workloads):
+        self.items = workloads.batch_spec(seed=4)
+        every = 16
+        self.imgs = [workloads.smooth_field_u8(it.seed, it.H, it.W, 3) if k % every == 0 else None
+                     for k, it in enumerate(self.items)]
+
 
 def run_reference(args, rank, world):
     if rank != 0:
@@ -606,41 +677,27 @@ def run_reference(args, rank, world):
     from oracle import oracle
     from paper_1001_1718_gb300 import workloads
     oracle.build()
-    img = workloads.workload_rgb_4096(seed=2)
-    x = img.astype(np.float64)
-    H, W, C = img.shape
-    band = 32
-    jobs = []
-    for name, method, s in HEADLINE_OPS:
-        Ho, Wo = out_hw(H, s), out_hw(W, s)
-        jobs.append((Ho, Wo, {"nearest": 0, "bilinear": 1, "bicubic": 2}[method]))
+    hb = _HostBatch(workloads)
+    per_step = 32   # bands of 16 output rows per step
 
-    def step(k):
-        px = 0
-        for (Ho, Wo, code) in jobs:
-            y0 = (k * 131 * band) % (Ho - band)
-            ys = np.repeat(np.arange(y0, y0 + band), Wo)
-            xs = np.tile(np.arange(Wo), band)
-            oracle.resize_points(x, Ho, Wo, code, 0, -0.5, ys, xs)
-            px += len(ys)
-        return px
-
+    for idx in range(0, len(hb.items), 16):   # the FP64 copies, before any step
+        hb.f64 = getattr(hb, "f64", {})
+        hb.f64[idx] = hb.imgs[idx].astype(np.float64)
     for k in range(args.warmup):
-        step(k)
-    t0 = time.perf_counter()
-    px = 0
+        _oracle_batch_sample(oracle, hb, 1e9, max_steps=per_step)
+    px, dt, bands, npk = 0, 0.0, 0, 0
     for k in range(args.steps):
-        px += step(k)
-    dt = time.perf_counter() - t0
+        p, d, nb, npk = _oracle_batch_sample(oracle, hb, 1e9, max_steps=per_step)
+        px, dt, bands = px + p, dt + d, bands + nb
     value = px / dt / 1e9
-    sample = (f"each step: {band} output rows of each of bicubic x2, bicubic x1.7, nearest x2 "
-              f"({px // max(1, args.steps)} output px per step)")
+    sample = (f"each step: {per_step} bands of 16 output rows of the batch images, round robin over {npk} of "
+              f"the 256 images ({px // max(1, args.steps)} output px per step)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpixels/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(1, args.steps) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "rgb_u8_4096x4096_smooth_field: bicubic x2, bicubic x1.7, nearest x2",
-                       "storage": "u8 HWC interleaved, C=3", "coord": "asymmetric (Eq. 1)", "cubic_a": -0.5,
+            "config": {"workload": BATCH_WORKLOAD, "images": 256, "storage": "u8 HWC interleaved, C=3",
+                       "coord": "asymmetric (Eq. 1)", "cubic_a": -0.5,
                        "kernel": "FP64 CPU oracle (direct per-pixel loops, OpenMP over points)"},
             "cpu_baseline": {"value": value, "unit": "Gpixels/s", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},

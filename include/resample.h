@@ -305,6 +305,9 @@ rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype,
                                  const rs_options* opt, void* stream,
                                  rs_batched_plan** plan);
 rs_status rs_batched_plan_launch(rs_batched_plan* plan, void* stream);
+/* Kernel launches one replay makes: one persistent launch per non-empty class
+ * (window items by method, channel count and footprint tier; tiles). */
+rs_status rs_batched_plan_kernels(const rs_batched_plan* plan, int32_t* kernels);
 rs_status rs_batched_plan_destroy(rs_batched_plan* plan);
 
 /*

@@ -291,6 +291,12 @@ class BatchedPlan:
                                                  ctypes.byref(o), _stream(srcs[0]), ctypes.byref(self._plan)),
                     "rs_batched_plan_create")
 
+    def kernels(self) -> int:
+        """Kernel launches one replay makes (one per non-empty class)."""
+        n = ctypes.c_int32(0)
+        B.check(lib().rs_batched_plan_kernels(self._plan, ctypes.byref(n)), "rs_batched_plan_kernels")
+        return n.value
+
     def launch(self, stream: int | None = None) -> None:
         with torch.cuda.device(self.device):
             st = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream

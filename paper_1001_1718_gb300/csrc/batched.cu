@@ -577,6 +577,7 @@ struct rs_batched_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
+    int kernels = 0;   // kernel launches per replay (one per non-empty class)
 };
 
 extern "C" {
@@ -649,6 +650,7 @@ rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype, 
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, p->graph, nullptr, 0, &kp);
     }
+    p->kernels = nl;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
     if (e != cudaSuccess) {
         if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -664,6 +666,13 @@ rs_status rs_batched_plan_launch(rs_batched_plan* plan, void* stream)
 {
     if (!plan || !plan->exec) return RS_ERR_INVALID_ARG;
     return cuda_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+}
+
+rs_status rs_batched_plan_kernels(const rs_batched_plan* plan, int32_t* kernels)
+{
+    if (!plan || !kernels) return RS_ERR_INVALID_ARG;
+    *kernels = plan->kernels;
+    return RS_OK;
 }
 
 rs_status rs_batched_plan_destroy(rs_batched_plan* plan)
