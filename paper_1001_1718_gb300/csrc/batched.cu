@@ -47,6 +47,7 @@ struct BatchImage {
 static constexpr int kClasses = 17;
 static constexpr int kTileClass = 16;
 static constexpr size_t kWindowSmallSmem = 72 * 1024;
+static constexpr int kHeavyBand = 32;   // band rows of large-footprint and downscaled window items
 
 __device__ __forceinline__ int find_image(const int64_t* __restrict__ start, int n, int64_t t)
 {
@@ -219,7 +220,11 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
             if (!win_config(g, x.method, dtype, wc, false) || wc.smem > (t < 2 ? kWindowSmallSmem : 100 * 1024)) continue;
             im.kind = 1;
             im.chunk = wc.chunk;
-            im.band_h = std::min(wc.band_cap, sh.band);
+            // A large footprint or a vertical downscale makes each band row
+            // costly (more source rows staged per output row): short bands
+            // spread such images over many blocks instead of a few long ones.
+            const bool heavy = t >= 2 || x.Ho < x.H;
+            im.band_h = std::min(wc.band_cap, heavy ? std::min(sh.band, kHeavyBand) : sh.band);
             im.swe = wc.swe;
             im.band_cap = wc.band_cap;
             im.pos_cap = wc.pos_cap;
