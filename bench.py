@@ -630,6 +630,45 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak, b):
         note="one replay of a CUDA graph holding the resize (device time, L2 flushed before)")
     del graph
 
+    # --- the fused serving pre-process (resample + per-channel normalise +
+    # HWC uint8 -> planar FP16) against the unfused path: the library's
+    # uint8 resize, then torch's permute / normalise / cast
+    mean_t, std_t = (123.675, 116.28, 103.53), (58.395, 57.12, 57.375)
+    for name, (N, H, W), (Ho, Wo), method in (("frames32_1024_to_512_bilinear", (32, 1024, 1024), (512, 512), "bilinear"),
+                                              ("frames32_512_to_1024_bicubic", (32, 512, 512), (1024, 1024), "bicubic"),
+                                              ("frames16_1080p_to_256x455_bilinear", (16, 1080, 1920), (256, 455),
+                                               "bilinear")):
+        frames = np.stack([workloads.smooth_field_u8(600 + k, H, W, 3) for k in range(N)])
+        xf = torch.from_numpy(frames).to(dev)
+        yo = torch.empty((N, 3, Ho, Wo), dtype=torch.float16, device=dev)
+        try:
+            rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo)
+        except rs.ResampleError as e:
+            ex[f"normalize_{name}"] = {"unsupported": str(e)}
+            continue
+        ms_f = bench(lambda: rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo), 20)
+        yu8 = torch.empty((N, Ho, Wo, 3), dtype=torch.uint8, device=dev)
+        mt = torch.tensor(mean_t, device=dev).view(1, 3, 1, 1)
+        st = torch.tensor(std_t, device=dev).view(1, 3, 1, 1)
+
+        def unfused():
+            rs.resize(xf, (Ho, Wo), method, out=yu8)
+            torch.sub(yu8.permute(0, 3, 1, 2).float(), mt).div_(st).to(torch.float16)
+        ms_u = bench(unfused, 20)
+        k0 = 0
+        ys, xs = workloads.sample_points(5, Ho, Wo, 2048)
+        ref = oracle.resize_normalize(frames[k0].astype(np.float64), Ho, Wo, rs.METHODS[method], mean_t, std_t)
+        got = yo[k0][:, torch_index(ys), torch_index(xs)].double().cpu().numpy()
+        refp = ref[:, ys, xs]
+        unf = ((yu8[k0].permute(2, 0, 1).double() - mt[0].double()) / st[0].double())[:, torch_index(ys), torch_index(xs)]
+        rec(f"normalize_{name}_fused_f16", ms_f, xf.numel(), yo.numel() * 2, N * Ho * Wo,
+            unfused_ms=ms_u, speedup_vs_unfused=ms_u / ms_f,
+            max_abs_vs_f64=float(np.abs(got - refp).max()),
+            unfused_max_abs_vs_f64_before_f16=float(np.abs(unf.cpu().numpy() - refp).max()),
+            note="one pass: uint8 HWC in, FP16 NCHW out; unfused: uint8 resize, then permute / normalise / cast")
+        del xf, yo, yu8
+    torch.cuda.empty_cache()
+
     # --- NCHW FP32 32x3x512x512: forward and backward, x2 and x0.5
     xn = torch.from_numpy(workloads.workload_nchw_512(seed=5).astype(np.float32)).to(dev)
     for method in ("bilinear", "bicubic"):

@@ -192,6 +192,27 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
                        const rs_options* opt, void* stream);
 
 /*
+ * Fused serving pre-process (an extension of Sec. II.B, Eqs. 1-5): resample
+ * a uint8 interleaved batch (in: N images of H x W x C, C <= 4, any pitches)
+ * bilinearly or bicubically, normalise every channel, y = (x - mean[c]) /
+ * stddev[c], and store it planar (out: N x C x Ho x Wo, px_stride 1; for C = 1
+ * either layout) as RS_F16, RS_BF16 or RS_F32, rounded to nearest even --
+ * one pass over the source and one over the output, where a resize followed
+ * by a separate normalise-and-transpose pass reads and writes the image
+ * twice and rounds it to uint8 in between. The resampled value stays FP32
+ * (it is never rounded to uint8); the normalisation is one FP32 fused
+ * multiply-add per element with scale 1 / stddev[c] and bias -mean[c] /
+ * stddev[c]. mean, stddev: C host floats each (finite, stddev nonzero). Options: coord and
+ * cubic_a as for rs_resize_ex; impl RS_IMPL_AUTO or RS_IMPL_WINDOW (the
+ * register-window kernel; tile_h = staged rows per chunk, waves); flags 0.
+ * RS_NEAREST returns RS_ERR_UNSUPPORTED, and so does a downscale whose
+ * staged footprint exceeds shared memory (about 1/5 and below).
+ */
+rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, const rs_layout* out,
+                              rs_dtype out_dtype, rs_method method, const float* mean, const float* stddev,
+                              const rs_options* opt, void* stream);
+
+/*
  * Backward (adjoint) of rs_resize_ex for RS_F32: grad_in = A^T grad_out,
  * where A is the linear map the forward applies (per axis, the transpose of
  * the interpolation weights, summed over the clamped taps). Computed in

@@ -124,6 +124,27 @@ def resize_nchw(x, Ho: int, Wo: int, method: int, coord: int = ASYMMETRIC,
     return np.ascontiguousarray(y.transpose(2, 0, 1).reshape(N, C, Ho, Wo))
 
 
+def resize_normalize(src, Ho: int, Wo: int, method: int, mean, std, coord: int = ASYMMETRIC,
+                     a: float = -0.5) -> np.ndarray:
+    """The serving pre-process in FP64: resample an (H, W, C) or (N, H, W, C)
+    interleaved image (Eqs. 1-5, as resize), then normalise each channel,
+    (y - mean[c]) / std[c], and return planar (C, Ho, Wo) or (N, C, Ho, Wo).
+    Nothing is rounded in between (the fused pass never stores the resampled
+    value); round the result with store() for a storage dtype."""
+    x = np.asarray(src, np.float64)
+    batched = x.ndim == 4
+    if not batched:
+        x = x[None]
+    N, H, W, C = x.shape
+    m = np.asarray(mean, np.float64).reshape(C)
+    s = np.asarray(std, np.float64).reshape(C)
+    out = np.empty((N, C, Ho, Wo), np.float64)
+    for n in range(N):
+        y = resize(x[n], Ho, Wo, method, coord, a)          # (Ho, Wo, C)
+        out[n] = ((y - m) / s).transpose(2, 0, 1)
+    return out if batched else out[0]
+
+
 def bilinear_eq5(src2d, Ho: int, Wo: int) -> np.ndarray:
     x = np.ascontiguousarray(src2d, np.float64)
     H, W = x.shape

@@ -30,7 +30,7 @@ IMPL_NAMES = {v: k for k, v in IMPLS.items()}
 DTYPES = {torch.uint8: B.RS_U8, torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16,
           torch.float32: B.RS_F32}
 
-__all__ = ["resize", "resize_backward", "ResizeFn", "resize_batched", "BatchedPlan", "autotune", "autotune_batched",
+__all__ = ["resize", "resize_normalize", "resize_backward", "ResizeFn", "resize_batched", "BatchedPlan", "autotune", "autotune_batched",
            "tile_config", "tune_cache_save", "tune_cache_load", "tune_cache_clear", "debug_fault",
            "version", "lib", "ResampleError", "METHODS", "COORDS"]
 
@@ -163,6 +163,44 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
         B.check(lib().rs_resize_ex(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo),
                                    _dtype(x), _code(METHODS, method, "method"), ctypes.byref(o),
                                    _stream(x)), "rs_resize_ex")
+    return out
+
+
+_OUT_DTYPES = {torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16, torch.float32: B.RS_F32}
+
+
+def resize_normalize(x: torch.Tensor, size: Sequence[int], method="bilinear", mean=(0.0, 0.0, 0.0),
+                     std=(1.0, 1.0, 1.0), *, dtype=torch.float16, coord="asymmetric", cubic_a: float = -0.5,
+                     out: torch.Tensor | None = None, impl="auto", chunk: int = 0) -> torch.Tensor:
+    """The fused serving pre-process: resample a uint8 (H, W, C) or
+    (N, H, W, C) image, normalise every channel, (y - mean[c]) / std[c], and
+    return it planar, (C, Ho, Wo) or (N, C, Ho, Wo), as FP16 / BF16 / FP32,
+    in one pass (rs_resize_normalize)."""
+    _require_cuda(x)
+    if x.dtype != torch.uint8:
+        raise ValueError("resize_normalize reads uint8 images")
+    try:
+        odt = _OUT_DTYPES[dtype]
+    except KeyError:
+        raise ValueError(f"unsupported output dtype {dtype}") from None
+    Ho, Wo = int(size[0]), int(size[1])
+    batched = x.dim() == 4
+    C = x.shape[-1]
+    shape = (x.shape[0], C, Ho, Wo) if batched else (C, Ho, Wo)
+    if out is None:
+        out = torch.empty(shape, dtype=dtype, device=x.device)
+    elif tuple(out.shape) != shape or out.dtype != dtype:
+        raise ValueError(f"out must be {shape} of {dtype}")
+    Li, Lo = _layout(x, "hwc"), _layout(out, "nchw")
+    if len(mean) != C or len(std) != C:
+        raise ValueError("mean and std need one value per channel")
+    m = (ctypes.c_float * C)(*[float(v) for v in mean])
+    s = (ctypes.c_float * C)(*[float(v) for v in std])
+    o = _opts(coord, cubic_a, impl, (0, chunk), 0)
+    with _on_device(x):
+        B.check(lib().rs_resize_normalize(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo), odt,
+                                          _code(METHODS, method, "method"), m, s, ctypes.byref(o), _stream(x)),
+                "rs_resize_normalize")
     return out
 
 

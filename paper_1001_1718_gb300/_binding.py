@@ -71,6 +71,9 @@ SIGNATURES = {
     "rs_batched_plan_create": (I32, [ctypes.POINTER(RsImageDesc), I32, I32, P, SZ, ctypes.POINTER(RsOptions),
                                      P, ctypes.POINTER(P)]),
     "rs_batched_plan_launch": (I32, [P, P]),
+    "rs_resize_normalize": (I32, [P, ctypes.POINTER(RsLayout), P, ctypes.POINTER(RsLayout), I32, I32,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(RsOptions), P]),
     "rs_batched_plan_kernels": (I32, [P, ctypes.POINTER(I32)]),
     "rs_batched_plan_destroy": (I32, [P]),
     "rs_autotune": (I32, [P, ctypes.POINTER(RsLayout), P, ctypes.POINTER(RsLayout), I32, I32,

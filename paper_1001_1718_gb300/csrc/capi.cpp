@@ -184,6 +184,63 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst, const rs
     return cuda_status(launch_choice(g, method, dtype, src, dst, k, st));
 }
 
+rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, const rs_layout* out,
+                              rs_dtype out_dtype, rs_method method, const float* mean, const float* stddev,
+                              const rs_options* opt, void* stream)
+{
+    const rs_options o = options_or_default(opt);
+    if (!src || !dst || !mean || !stddev || !in || !out) return RS_ERR_INVALID_ARG;
+    if (out_dtype != RS_F16 && out_dtype != RS_BF16 && out_dtype != RS_F32) return RS_ERR_INVALID_ARG;
+    rs_status s = check_options(o, method);
+    if (s != RS_OK) return s;
+    if (method == RS_NEAREST) return RS_ERR_UNSUPPORTED;
+    if (o.flags || (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) || o.tile_w || o.threads) return RS_ERR_INVALID_ARG;
+    LayoutInfo li, lo;
+    if ((s = classify(in, li)) != RS_OK) return s;
+    if ((s = classify(out, lo)) != RS_OK) return s;
+    // interleaved source, planar output (for one channel the two coincide)
+    if (li.kind != 0 || (in->C > 1 && lo.kind != 1) || in->N != out->N || in->C != out->C) return RS_ERR_INVALID_ARG;
+    NormOut no;
+    no.c_stride = out->c_stride;
+    for (int c = 0; c < 4; ++c) {
+        no.scale[c] = 1.0f;
+        no.bias[c] = 0.0f;
+    }
+    for (int c = 0; c < in->C; ++c) {
+        if (!std::isfinite(mean[c]) || !std::isfinite(stddev[c]) || stddev[c] == 0.0f) return RS_ERR_INVALID_ARG;
+        no.scale[c] = 1.0f / stddev[c];
+        no.bias[c] = -mean[c] / stddev[c];
+        if (!std::isfinite(no.scale[c]) || !std::isfinite(no.bias[c])) return RS_ERR_INVALID_ARG;
+    }
+    const size_t eo = dtype_size(out_dtype);
+    if (reinterpret_cast<uintptr_t>(dst) % eo) return RS_ERR_ALIGNMENT;
+    if (overlaps(src, li.extent, dst, lo.extent * (int64_t)eo)) return RS_ERR_INVALID_ARG;
+    Geom g;
+    g.H = in->H; g.W = in->W; g.Ho = out->H; g.Wo = out->W;
+    g.C = in->C;
+    g.src_pitch = in->row_pitch;
+    g.dst_pitch = out->row_pitch;
+    g.sp = PlaneMap{in->n_stride, 0, 1};
+    g.dp = PlaneMap{out->n_stride, 0, 1};
+    g.planes = in->N;
+    g.coord = o.coord;
+    g.a = o.cubic_a;
+    // the window kernel: chunks of 8 staged rows, else 4 (larger footprints)
+    WinCfg c{};
+    c.waves = o.waves;
+    bool ok = false;
+    for (int ch : {o.tile_h ? o.tile_h : 8, o.tile_h ? 0 : 4}) {
+        if (!ch) continue;
+        c.chunk = ch;
+        if (win_config(g, method, DT_U8, c)) {
+            ok = true;
+            break;
+        }
+    }
+    if (!ok) return o.tile_h ? RS_ERR_INVALID_ARG : RS_ERR_UNSUPPORTED;
+    return cuda_status(launch_win_norm(g, method, out_dtype, src, dst, c, no, static_cast<cudaStream_t>(stream)));
+}
+
 rs_status rs_resize(const void* src, int H, int W, int C, rs_dtype dtype, void* dst, int Ho, int Wo,
                     rs_method method, void* stream)
 {

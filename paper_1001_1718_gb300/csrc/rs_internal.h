@@ -110,6 +110,15 @@ struct WinCfg {
     size_t smem;
 };
 
+// Output of the fused pre-process (rs_resize_normalize): planar channels,
+// channel c of an image at c * c_stride elements from its first element;
+// each value is the resampled FP32 value times scale[c] plus bias[c]
+// (scale = 1 / std, bias = -mean / std), rounded to the output dtype.
+struct NormOut {
+    int64_t c_stride;
+    float scale[4], bias[4];
+};
+
 int method_taps(int method);
 size_t dtype_size(int dtype);
 
@@ -147,6 +156,11 @@ int win_pixels(int C, int dtype, bool x2);
 bool win_is_x2(const Geom& g);
 bool win_config(const Geom& g, int method, int dtype, WinCfg& c, bool allow_x2 = true);
 cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, void* dst, WinCfg c, cudaStream_t st);
+// The fused pre-process on the window kernels: uint8 interleaved source
+// (g describes it; g.dp / g.dst_pitch the output images and rows),
+// normalised planar output of out_dtype (DT_F16, DT_BF16 or DT_F32).
+cudaError_t launch_win_norm(const Geom& g, int method, int out_dtype, const void* src, void* dst, WinCfg c,
+                            const NormOut& no, cudaStream_t st);
 bool nearest_config(const Geom& g, int dtype, int tile_w, int rows_per_thread);
 int nearest_default_rows(const Geom& g, int dtype);
 cudaError_t launch_nearest(const Geom& g, int dtype, const void* src, void* dst, int tile_w, int rows_per_thread,

@@ -165,6 +165,51 @@ __device__ __forceinline__ void win_store_run(T* p, const uint32_t (&w)[WinShape
     }
 }
 
+// Fused pre-process (X2): P values of one channel plane, rounded to TO and
+// packed into words in memory order.
+template <int P, typename TO>
+__device__ __forceinline__ void win_pack_plane(const float (&y)[P], uint32_t (&w)[P * sizeof(TO) / 4])
+{
+    if constexpr (sizeof(TO) == 4) {
+        #pragma unroll
+        for (int k = 0; k < P; ++k) w[k] = __float_as_uint(y[k]);
+    } else {
+        #pragma unroll
+        for (int q = 0; q < P / 2; ++q) {
+            if constexpr (std::is_same<TO, __half>::value) {
+                const __half2 h = __floats2half2_rn(y[2 * q], y[2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t*>(&h);
+            } else {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(y[2 * q], y[2 * q + 1]);
+                w[q] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+        }
+    }
+}
+
+// NW words at p with the widest stores its alignment (align bytes) allows.
+template <int NW, typename TO>
+__device__ __forceinline__ void win_store_words(TO* p, const uint32_t (&w)[NW], int align)
+{
+    if (NW % 4 == 0 && align >= 16) {
+        #pragma unroll
+        for (int q = 0; q < NW / 4; ++q)
+            reinterpret_cast<uint4*>(p)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    } else if (NW % 2 == 0 && align >= 8) {
+        #pragma unroll
+        for (int q = 0; q < NW / 2; ++q) reinterpret_cast<uint2*>(p)[q] = make_uint2(w[2 * q], w[2 * q + 1]);
+    } else if (align >= 4) {
+        #pragma unroll
+        for (int q = 0; q < NW; ++q) reinterpret_cast<uint32_t*>(p)[q] = w[q];
+    } else {
+        #pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            reinterpret_cast<uint16_t*>(p)[2 * q] = (uint16_t)w[q];
+            reinterpret_cast<uint16_t*>(p)[2 * q + 1] = (uint16_t)(w[q] >> 16);
+        }
+    }
+}
+
 // X2: the first n elements of a run, one by one (the strip's ragged end).
 template <int C, typename T>
 __device__ __forceinline__ void win_store_part(T* p, const float2 (&v)[WinShape<C, T, true>::NP][C], int n)
@@ -232,9 +277,9 @@ __device__ __forceinline__ void win_store_px(T* p, const float (&x)[C], bool vec
 // General form, the work of one block: strip bx and band by of one plane
 // (s, d point at the plane). Used by the single-image kernel and the batch's
 // persistent window kernels.
-template <int KT, int C, typename T>
-__device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s, T* __restrict__ d, const WinCfg& cfg,
-                                         int bx, int by, float* sm, unsigned int* fault)
+template <int KT, int C, typename T, typename TO = T, bool NORM = false>
+__device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s, TO* __restrict__ d, const WinCfg& cfg,
+                                         int bx, int by, float* sm, unsigned int* fault, const NormOut& no = NormOut{})
 {
     using S = WinShape<C, T, false>;
     constexpr int P = S::P, NP = S::NP, NT = kWinThreads;
@@ -422,15 +467,17 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
                 }
     };
 
-    // ---- output: one pixel's channels per store where the row allows it ----
+    // ---- output: one pixel's channels per store where the row allows it;
+    // the fused pre-process: channel c normalised into its own plane ----
     const int pitch32 = (int)g.dst_pitch;   // the host bounds band_cap * pitch < 2^31
-    T* const dband = d + (int64_t)yb * g.dst_pitch + (int64_t)j0 * C;
+    constexpr int EO = (int)sizeof(TO);
+    TO* const dband = d + (int64_t)yb * g.dst_pitch + (int64_t)j0 * (NORM ? 1 : C);
     constexpr int PB = C * ES;
-    constexpr bool can_vec = PB == 4 || PB == 8 || PB == 16 || (PB == 2 && ES == 1);
+    constexpr bool can_vec = !NORM && (PB == 4 || PB == 8 || PB == 16 || (PB == 2 && ES == 1));
     const bool vec0 = can_vec && (reinterpret_cast<uintptr_t>(dband) % PB) == 0;
-    const bool vec_all = ((g.dst_pitch * ES) % PB) == 0;   // every row keeps row 0's alignment
+    const bool vec_all = ((g.dst_pitch * EO) % PB) == 0;   // every row keeps row 0's alignment
     auto put = [&](int row, const float2 (&v)[NP][C]) {
-        T* p = dband + row * pitch32;
+        TO* p = dband + row * pitch32;
         const bool vec = can_vec && (vec_all ? vec0 : (reinterpret_cast<uintptr_t>(p) % PB) == 0);
         #pragma unroll
         for (int m = 0; m < P; ++m) {
@@ -438,7 +485,12 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
                 float x[C];
                 #pragma unroll
                 for (int c = 0; c < C; ++c) x[c] = (m & 1) ? v[m >> 1][c].y : v[m >> 1][c].x;
-                win_store_px<C, T>(p + 32 * m * C, x, vec);
+                if constexpr (NORM) {
+                    #pragma unroll
+                    for (int c = 0; c < C; ++c) Store<TO>::put(p + c * no.c_stride + 32 * m, fmaf(x[c], no.scale[c], no.bias[c]));
+                } else {
+                    win_store_px<C, T>(p + 32 * m * C, x, vec);
+                }
             }
         }
     };
@@ -528,9 +580,10 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
 // with two chunks in flight. Out-of-image footprint pixels (strips at the
 // image's left and right edges only) are written into the raw rows as copies
 // of the edge pixel once a chunk has landed.
-template <int KT, int C, typename T>
-__device__ __forceinline__ void win_body_x2(const Geom& g, const T* __restrict__ s, T* __restrict__ d,
-                                            const WinCfg& cfg, int bx, int by, float* sm, unsigned int* fault)
+template <int KT, int C, typename T, typename TO = T, bool NORM = false>
+__device__ __forceinline__ void win_body_x2(const Geom& g, const T* __restrict__ s, TO* __restrict__ d,
+                                            const WinCfg& cfg, int bx, int by, float* sm, unsigned int* fault,
+                                            const NormOut& no = NormOut{})
 {
     using S = WinShape<C, T, true>;
     constexpr int P = S::P, NP = S::NP, NT = kWinThreads;
@@ -670,23 +723,44 @@ __device__ __forceinline__ void win_body_x2(const Geom& g, const T* __restrict__
         }
     };
 
-    // ---- output: the run as 4-, 8- or 16-byte stores ----
+    // ---- output: the run as 4-, 8- or 16-byte stores; the fused
+    // pre-process: each channel's P values normalised into its own plane ----
     const int pitch32 = (int)g.dst_pitch;   // the host bounds band_cap * pitch < 2^31
-    T* const dband = d + (int64_t)yb * g.dst_pitch + (int64_t)j0 * C;
-    const bool same_align = ((g.dst_pitch * ES) & 15) == 0;   // every row keeps row 0's alignment
-    auto align_of = [&](const T* p) -> int {
+    constexpr int EO = (int)sizeof(TO);
+    TO* const dband = d + (int64_t)yb * g.dst_pitch + (int64_t)j0 * (NORM ? 1 : C);
+    const bool same_align = ((g.dst_pitch * EO) & 15) == 0 && (!NORM || ((no.c_stride * EO) & 15) == 0);
+    auto align_of = [&](const TO* p) -> int {
         const uintptr_t a = reinterpret_cast<uintptr_t>(p);
         return (a & 15) == 0 ? 16 : (a & 7) == 0 ? 8 : (a & 3) == 0 ? 4 : (a & 1) == 0 ? 2 : 1;
     };
     const int align0 = align_of(dband);
     auto put = [&](int row, const float2 (&v)[NP][C]) {
-        T* p = dband + row * pitch32;
-        if (nact == P) {
-            uint32_t w[S::NW];
-            win_pack<C, T>(v, w);
-            win_store_run<C, T>(p, w, same_align ? align0 : align_of(p));
-        } else if (nact > 0) {
-            win_store_part<C, T>(p, v, nact * C);
+        TO* p = dband + row * pitch32;
+        if constexpr (NORM) {
+            #pragma unroll
+            for (int c = 0; c < C; ++c) {
+                TO* pc = p + c * no.c_stride;
+                float y[P];
+                #pragma unroll
+                for (int k = 0; k < P; ++k) y[k] = fmaf((k & 1) ? v[k >> 1][c].y : v[k >> 1][c].x, no.scale[c], no.bias[c]);
+                if (nact == P && (P * EO) % 4 == 0) {
+                    uint32_t w[P * EO / 4];
+                    win_pack_plane<P, TO>(y, w);
+                    win_store_words<P * EO / 4>(pc, w, same_align ? align0 : align_of(pc));
+                } else {
+                    #pragma unroll
+                    for (int k = 0; k < P; ++k)
+                        if (k < nact) Store<TO>::put(pc + k, y[k]);
+                }
+            }
+        } else {
+            if (nact == P) {
+                uint32_t w[S::NW];
+                win_pack<C, T>(v, w);
+                win_store_run<C, T>(p, w, same_align ? align0 : align_of(p));
+            } else if (nact > 0) {
+                win_store_part<C, T>(p, v, nact * C);
+            }
         }
     };
 

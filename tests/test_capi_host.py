@@ -220,3 +220,31 @@ def test_product_path_refuses_cpu_tensors():
     import paper_1001_1718_gb300 as rs
     with pytest.raises(ValueError):
         rs.resize(torch.zeros(4, 4, 3, dtype=torch.uint8), (8, 8), "bilinear")
+
+
+def test_resize_normalize_validation(L):
+    """rs_resize_normalize checks its arguments on the host before anything
+    is launched (no GPU needed for these refusals)."""
+    from paper_1001_1718_gb300 import _binding as B
+    P, Q = 0x10000, 0x90000000      # never dereferenced
+    li, lo = L.rs_layout_hwc(2, 16, 16, 3), L.rs_layout_nchw(2, 3, 32, 32)
+    m = (ctypes.c_float * 3)(120.0, 110.0, 100.0)
+    sd = (ctypes.c_float * 3)(58.0, 57.0, 57.0)
+    bad_sd = (ctypes.c_float * 3)(58.0, 0.0, 57.0)
+
+    def call(src=P, inl=li, dst=Q, outl=lo, dt=B.RS_F16, meth=B.RS_BILINEAR, mean=m, std=sd, opt=None):
+        return L.rs_resize_normalize(src, ctypes.byref(inl), dst, ctypes.byref(outl), dt, meth, mean, std,
+                                     ctypes.byref(opt) if opt is not None else None, None)
+    assert call(src=0) == B.RS_ERR_INVALID_ARG
+    assert call(mean=None) == B.RS_ERR_INVALID_ARG
+    assert call(dt=B.RS_U8) == B.RS_ERR_INVALID_ARG               # outputs are FP16 / BF16 / FP32
+    assert call(meth=B.RS_NEAREST) == B.RS_ERR_UNSUPPORTED
+    assert call(std=bad_sd) == B.RS_ERR_INVALID_ARG               # a zero std
+    assert call(outl=L.rs_layout_hwc(2, 32, 32, 3)) == B.RS_ERR_INVALID_ARG   # the output must be planar
+    assert call(inl=L.rs_layout_nchw(2, 3, 16, 16)) == B.RS_ERR_INVALID_ARG   # the source must be interleaved
+    assert call(outl=L.rs_layout_nchw(1, 3, 32, 32)) == B.RS_ERR_INVALID_ARG  # N differs
+    assert call(opt=B.options(impl=B.RS_IMPL_TILED)) == B.RS_ERR_INVALID_ARG
+    o = B.options()
+    o.flags = B.RS_FLAG_ANTIALIAS
+    assert call(opt=o) == B.RS_ERR_INVALID_ARG
+    assert call(dst=Q + 1) == B.RS_ERR_ALIGNMENT                  # FP16 output on an odd address

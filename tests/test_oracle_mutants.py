@@ -2,8 +2,9 @@
 
 Each case plants one mistake in a copy of oracle/resample_oracle.c (on the
 CPU, in a temporary directory), builds it, and runs the pin suite against
-that build: the suite has to fail. Every planted mistake keeps all memory
-accesses in bounds.
+that build: the suite has to fail. The Python-layer cases plant the mistake
+in a copy of oracle/oracle.py instead (run against the real C library).
+Every planted mistake keeps all memory accesses in bounds.
 """
 import os
 import subprocess
@@ -34,6 +35,31 @@ MUTANTS = {
     "align_corners_denominator": ("        den = m - 1;\n", "        den = m;\n"),
     "align_corners_nearest_floor": ("i = floor_div(2 * num + den, 2 * den);", "i = floor_div(2 * num, 2 * den);"),
 }
+
+
+PY_SRC = ROOT / "oracle" / "oracle.py"
+PY_MUTANTS = {
+    "normalize_channel_order": ("out[n] = ((y - m) / s).transpose(2, 0, 1)",
+                                "out[n] = ((y - m[::-1]) / s).transpose(2, 0, 1)"),
+    "normalize_scale_not_divide": ("out[n] = ((y - m) / s).transpose(2, 0, 1)",
+                                   "out[n] = ((y - m) * (1.0 / s[0])).transpose(2, 0, 1)"),
+    "normalize_planar_axes": ("out[n] = ((y - m) / s).transpose(2, 0, 1)",
+                              "out[n] = ((y - m) / s).transpose(2, 1, 0).reshape(C, Ho, Wo)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_planted_python_mistake(name, tmp_path, oracle):
+    old, new = PY_MUTANTS[name]
+    text = PY_SRC.read_text()
+    assert text.count(old) == 1, name
+    src = tmp_path / "oracle_mutant.py"
+    src.write_text(text.replace(old, new))
+    env = dict(os.environ, RESAMPLE_ORACLE_PY=str(src), RESAMPLE_ORACLE_LIB=str(oracle.build()))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        str(ROOT / "tests" / "test_oracle_pins.py")],
+                       env=env, cwd=str(ROOT), capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

@@ -447,3 +447,42 @@ def test_aa_upscale_is_half_pixel_interpolation_inside(oracle, method):
     a = oracle.resize_aa(x, 100, 110, method)
     b = oracle.resize(x, 100, 110, method, 1)
     assert np.abs(a[10:-10, 10:-10] - b[10:-10, 10:-10]).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# The fused serving pre-process: resample, then (y - mean) / std per channel,
+# laid out planar. Pinned against torch's FP64 interpolate (half-pixel map,
+# Keys a = -3/4 for bicubic, its own implementation) followed by torch's own
+# normalise and permute.
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("shape", [(2, 13, 17, 3), (1, 9, 31, 4), (3, 20, 11, 1)])
+def test_resize_normalize_matches_torch(oracle, method, shape):
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    r = np.random.default_rng(77)
+    x = r.integers(0, 256, shape).astype(np.float64)
+    N, H, W, C = shape
+    mean = r.uniform(0, 255, C)
+    std = r.uniform(20, 90, C)
+    for Ho, Wo in ((2 * H + 1, W + 7), (max(1, H // 2), max(1, W // 3))):
+        got = oracle.resize_normalize(x, Ho, Wo, method, mean, std, coord=1, a=-0.75)
+        mode = "bilinear" if method == 1 else "bicubic"
+        t = F.interpolate(torch.from_numpy(x).permute(0, 3, 1, 2), size=(Ho, Wo), mode=mode, align_corners=False)
+        ref = ((t - torch.from_numpy(mean)[None, :, None, None]) / torch.from_numpy(std)[None, :, None, None]).numpy()
+        assert got.shape == (N, C, Ho, Wo)
+        assert np.abs(got - ref).max() < 1e-11, (method, shape, Ho, Wo)
+
+
+def test_resize_normalize_single_image_and_identity(oracle):
+    """An (H, W, C) image gives (C, Ho, Wo); at identity size with mean 0 and
+    std 1 the output is the input, transposed to planar, exactly."""
+    r = np.random.default_rng(78)
+    x = r.integers(0, 256, (7, 9, 3)).astype(np.float64)
+    y = oracle.resize_normalize(x, 7, 9, 2, [0, 0, 0], [1, 1, 1])
+    assert y.shape == (3, 7, 9)
+    assert np.array_equal(y, x.transpose(2, 0, 1))
+    # a constant channel maps to (value - mean) / std exactly (partition of unity)
+    c = np.full((5, 6, 2), 200.0)
+    y = oracle.resize_normalize(c, 11, 13, 2, [100.0, 50.0], [50.0, 25.0])
+    assert np.allclose(y[0], 2.0, atol=1e-13) and np.allclose(y[1], 6.0, atol=1e-13)
