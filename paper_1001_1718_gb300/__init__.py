@@ -171,11 +171,13 @@ _OUT_DTYPES = {torch.float16: B.RS_F16, torch.bfloat16: B.RS_BF16, torch.float32
 
 def resize_normalize(x: torch.Tensor, size: Sequence[int], method="bilinear", mean=(0.0, 0.0, 0.0),
                      std=(1.0, 1.0, 1.0), *, dtype=torch.float16, coord="asymmetric", cubic_a: float = -0.5,
-                     out: torch.Tensor | None = None, impl="auto", chunk: int = 0) -> torch.Tensor:
+                     out: torch.Tensor | None = None, impl="auto", chunk: int = 0,
+                     antialias: bool = False) -> torch.Tensor:
     """The fused serving pre-process: resample a uint8 (H, W, C) or
     (N, H, W, C) image, normalise every channel, (y - mean[c]) / std[c], and
     return it planar, (C, Ho, Wo) or (N, C, Ho, Wo), as FP16 / BF16 / FP32,
-    in one pass (rs_resize_normalize)."""
+    in one pass (rs_resize_normalize). antialias=True stretches the filter
+    by the downscale factor (RS_FLAG_ANTIALIAS, at most 8 taps per axis)."""
     _require_cuda(x)
     if x.dtype != torch.uint8:
         raise ValueError("resize_normalize reads uint8 images")
@@ -197,6 +199,8 @@ def resize_normalize(x: torch.Tensor, size: Sequence[int], method="bilinear", me
     m = (ctypes.c_float * C)(*[float(v) for v in mean])
     s = (ctypes.c_float * C)(*[float(v) for v in std])
     o = _opts(coord, cubic_a, impl, (0, chunk), 0)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     with _on_device(x):
         B.check(lib().rs_resize_normalize(x.data_ptr(), ctypes.byref(Li), out.data_ptr(), ctypes.byref(Lo), odt,
                                           _code(METHODS, method, "method"), m, s, ctypes.byref(o), _stream(x)),

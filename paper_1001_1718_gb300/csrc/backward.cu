@@ -381,62 +381,6 @@ struct AdjWinCfg {
     size_t smem;
 };
 
-// Antialias taps of output j of an axis of m outputs over n samples (the
-// definition in rs_resize_ex's RS_FLAG_ANTIALIAS): the kernel stretched by
-// f = max(n / m, 1), taps cut to [0, n), weights renormalised. In exact
-// integer arithmetic with F = max(n, m) = m f: the centre is
-// c = (2j + 1) n / (2m), so the taps run from floor(((2j+1) n - 2 R F + m) /
-// (2m)) to floor(((2j+1) n + 2 R F + m) / (2m)) - 1, and tap i sits at
-// u = ((2i+1) m - (2j+1) n) / (2F) kernel units. (Where that bound is an
-// exact integer an FP64 evaluation may add or drop the boundary tap; its
-// weight K(+-R) is zero.) The weights are evaluated in FP32.
-__host__ __device__ inline int64_t floor_div_i64(int64_t a, int64_t b)   // b > 0
-{
-    const int64_t q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
-
-__host__ __device__ inline void aa_range(int j, int n, int m, int method, int& lo, int& hi)
-{
-    const int64_t R = method == M_BILINEAR ? 1 : 2;
-    const int64_t F = n > m ? n : m;
-    const int64_t a = (int64_t)(2 * j + 1) * n + m;
-    const int64_t l = floor_div_i64(a - 2 * R * F, 2 * (int64_t)m);
-    const int64_t h = floor_div_i64(a + 2 * R * F, 2 * (int64_t)m);
-    lo = (int)(l < 0 ? 0 : l);
-    hi = (int)(h > n ? n : h);   // exclusive
-}
-
-template <int K>
-__device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a, int& lo, float* w,
-                                        unsigned int* fault)
-{
-    int hi;
-    aa_range(j, n, m, method, lo, hi);
-    int cnt = max(0, hi - lo);
-    if (cnt > K) {   // excluded by the host
-        report_fault(fault, FAULT_BWD_TAPS);
-        cnt = K;
-    }
-    const float inv2F = 1.0f / (2.0f * (float)max(n, m));
-    const int64_t cj = (int64_t)(2 * j + 1) * n;
-    float tot = 0.0f;
-    #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        float v = 0.0f;
-        if (k < cnt) {
-            const float u = fabsf((float)((int64_t)(2 * (lo + k) + 1) * m - cj) * inv2F);
-            if (method == M_BILINEAR) v = fmaxf(0.0f, 1.0f - u);
-            else if (u <= 1.0f) v = ((a + 2.0f) * u - (a + 3.0f)) * u * u + 1.0f;
-            else if (u < 2.0f) v = ((a * u - 5.0f * a) * u + 8.0f * a) * u - 4.0f * a;
-        }
-        w[k] = v;
-        tot += v;
-    }
-    const float inv = tot != 0.0f ? 1.0f / tot : 1.0f;
-    #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] *= inv;
-}
 // Threads per block: 256 (strips of 512 dX elements), or 128 (strips of
 // 256) for the computed-tap modes where that pads narrow rows less.
 static constexpr int kAwThreads = 256;
@@ -834,24 +778,61 @@ static AxisRanges aa_ranges(int n, int m, int method)
     return R;
 }
 
+// The antialiased window form's configuration: K = 4 or 8 taps per axis,
+// chunks of 8 staged rows, else 4 (K = 4: large FP32 footprints), else 16.
+static bool aa_window_setup(const Geom& gf, int method, int dtype, int& K, WinCfg& c)
+{
+    const int k = antialias_taps(gf, method);
+    K = k <= 4 ? 4 : k <= 8 ? 8 : 0;
+    if (!K) return false;
+    for (int ch : {8, 4, 16}) {
+        if (ch % K) continue;
+        c = WinCfg{};
+        c.chunk = ch;
+        if (win_config_aa(gf, method, dtype, K, c)) return true;
+    }
+    return false;
+}
+
 rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* src, void* dst, const rs_options& o,
                            cudaStream_t st)
 {
-    if (dtype != DT_F32) return RS_ERR_UNSUPPORTED;
     if (method != M_BILINEAR && method != M_BICUBIC) return RS_ERR_INVALID_ARG;
-    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) return RS_ERR_INVALID_ARG;
-    const Geom g = forward_as_adjoint(gf);
-    BwdPlan p;
-    p.ry = aa_ranges(gf.H, gf.Ho, method);
-    p.rx = aa_ranges(gf.W, gf.Wo, method);
-    p.yK = std::max(1, p.ry.kmax);
-    p.xK = std::max(1, p.rx.kmax);
-    AdjWinCfg c;
-    if (!adj_window_config(g, p, src, c, true)) return RS_ERR_UNSUPPORTED;
-    c.tap_method = method;
-    c.tap_a = o.cubic_a;
-    return cuda_status(launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst), AdjTables{},
-                                         c, st, TAPS_AA));
+    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW && o.impl != RS_IMPL_REDUCE) return RS_ERR_INVALID_ARG;
+    if (dtype == DT_F32 && o.impl != RS_IMPL_WINDOW) {
+        // FP32: the fused pass in its transposed roles reads the rows in place
+        const Geom g = forward_as_adjoint(gf);
+        BwdPlan p;
+        p.ry = aa_ranges(gf.H, gf.Ho, method);
+        p.rx = aa_ranges(gf.W, gf.Wo, method);
+        p.yK = std::max(1, p.ry.kmax);
+        p.xK = std::max(1, p.rx.kmax);
+        AdjWinCfg c;
+        if (adj_window_config(g, p, src, c, true)) {
+            c.tap_method = method;
+            c.tap_a = o.cubic_a;
+            return cuda_status(launch_adj_window(g, p, static_cast<const float*>(src), static_cast<float*>(dst),
+                                                 AdjTables{}, c, st, TAPS_AA));
+        }
+        if (o.impl == RS_IMPL_REDUCE) return RS_ERR_UNSUPPORTED;
+    }
+    if (o.impl == RS_IMPL_REDUCE) return RS_ERR_UNSUPPORTED;
+    // any dtype: the general window form with antialias taps
+    int K = 0;
+    WinCfg c;
+    if (!aa_window_setup(gf, method, dtype, K, c)) return RS_ERR_UNSUPPORTED;
+    c.waves = o.waves;
+    return cuda_status(launch_win_aa(gf, method, dtype, src, dst, K, c, st));
+}
+
+rs_status resize_normalize_antialias(const Geom& g, int method, int out_dtype, const void* src, void* dst,
+                                     const NormOut& no, const rs_options& o, cudaStream_t st)
+{
+    int K = 0;
+    WinCfg c;
+    if (!aa_window_setup(g, method, DT_U8, K, c)) return RS_ERR_UNSUPPORTED;
+    c.waves = o.waves;
+    return cuda_status(launch_win_aa_norm(g, method, out_dtype, src, dst, K, c, no, st));
 }
 
 // Host ranges of the point taps in the window pass's forward roles: rows

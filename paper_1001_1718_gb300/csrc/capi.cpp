@@ -194,7 +194,8 @@ rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, c
     rs_status s = check_options(o, method);
     if (s != RS_OK) return s;
     if (method == RS_NEAREST) return RS_ERR_UNSUPPORTED;
-    if (o.flags || (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) || o.tile_w || o.threads) return RS_ERR_INVALID_ARG;
+    if ((o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW) || o.tile_w || o.threads) return RS_ERR_INVALID_ARG;
+    if ((o.flags & RS_FLAG_ANTIALIAS) && o.tile_h) return RS_ERR_INVALID_ARG;
     LayoutInfo li, lo;
     if ((s = classify(in, li)) != RS_OK) return s;
     if ((s = classify(out, lo)) != RS_OK) return s;
@@ -225,6 +226,8 @@ rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, c
     g.planes = in->N;
     g.coord = o.coord;
     g.a = o.cubic_a;
+    if (o.flags & RS_FLAG_ANTIALIAS)
+        return resize_normalize_antialias(g, method, out_dtype, src, dst, no, o, static_cast<cudaStream_t>(stream));
     // the window kernel: chunks of 8 staged rows, else 4 (larger footprints)
     WinCfg c{};
     c.waves = o.waves;

@@ -44,6 +44,9 @@ cudaError_t read_fault(cudaStream_t st, unsigned int* code);
 // computed taps).
 rs_status resize_antialias(const Geom& g, int method, int dtype, const void* src, void* dst, const rs_options& o,
                            cudaStream_t st);
+// The fused pre-process with RS_FLAG_ANTIALIAS (the antialiased window form).
+rs_status resize_normalize_antialias(const Geom& g, int method, int out_dtype, const void* src, void* dst,
+                                     const NormOut& no, const rs_options& o, cudaStream_t st);
 // RS_IMPL_REDUCE forward (backward.cu: the fused window pass with the
 // point taps of Eqs. 1-5 computed in the kernel). reduce_config: whether it
 // applies, and its dynamic shared memory.

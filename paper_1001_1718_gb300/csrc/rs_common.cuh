@@ -177,4 +177,61 @@ __device__ __forceinline__ void report_fault(unsigned int* fault, unsigned int c
     if (fault) atomicCAS(fault, 0u, code);
 }
 
+// Antialias taps of output j of an axis of m outputs over n samples (the
+// definition in rs_resize_ex's RS_FLAG_ANTIALIAS): the kernel stretched by
+// f = max(n / m, 1), taps cut to [0, n), weights renormalised. In exact
+// integer arithmetic with F = max(n, m) = m f: the centre is
+// c = (2j + 1) n / (2m), so the taps run from floor(((2j+1) n - 2 R F + m) /
+// (2m)) to floor(((2j+1) n + 2 R F + m) / (2m)) - 1, and tap i sits at
+// u = ((2i+1) m - (2j+1) n) / (2F) kernel units. (Where that bound is an
+// exact integer an FP64 evaluation may add or drop the boundary tap; its
+// weight K(+-R) is zero.) The weights are evaluated in FP32.
+__host__ __device__ inline int64_t floor_div_i64(int64_t a, int64_t b)   // b > 0
+{
+    const int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+__host__ __device__ inline void aa_range(int j, int n, int m, int method, int& lo, int& hi)
+{
+    const int64_t R = method == M_BILINEAR ? 1 : 2;
+    const int64_t F = n > m ? n : m;
+    const int64_t a = (int64_t)(2 * j + 1) * n + m;
+    const int64_t l = floor_div_i64(a - 2 * R * F, 2 * (int64_t)m);
+    const int64_t h = floor_div_i64(a + 2 * R * F, 2 * (int64_t)m);
+    lo = (int)(l < 0 ? 0 : l);
+    hi = (int)(h > n ? n : h);   // exclusive
+}
+
+template <int K>
+__device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a, int& lo, float* w,
+                                        unsigned int* fault)
+{
+    int hi;
+    aa_range(j, n, m, method, lo, hi);
+    int cnt = max(0, hi - lo);
+    if (cnt > K) {   // excluded by the host
+        report_fault(fault, FAULT_BWD_TAPS);
+        cnt = K;
+    }
+    const float inv2F = 1.0f / (2.0f * (float)max(n, m));
+    const int64_t cj = (int64_t)(2 * j + 1) * n;
+    float tot = 0.0f;
+    #pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float v = 0.0f;
+        if (k < cnt) {
+            const float u = fabsf((float)((int64_t)(2 * (lo + k) + 1) * m - cj) * inv2F);
+            if (method == M_BILINEAR) v = fmaxf(0.0f, 1.0f - u);
+            else if (u <= 1.0f) v = ((a + 2.0f) * u - (a + 3.0f)) * u * u + 1.0f;
+            else if (u < 2.0f) v = ((a * u - 5.0f * a) * u + 8.0f * a) * u - 4.0f * a;
+        }
+        w[k] = v;
+        tot += v;
+    }
+    const float inv = tot != 0.0f ? 1.0f / tot : 1.0f;
+    #pragma unroll
+    for (int k = 0; k < K; ++k) w[k] *= inv;
+}
+
 }  // namespace rs

@@ -107,6 +107,8 @@ struct WinCfg {
     int pos_cap;     // source positions of a band
     int tab_off;     // byte offset of the row-tap tables in shared memory
     int raw_off;     // byte offset of the raw ring in shared memory
+    int aa_method;   // antialias taps: M_BILINEAR / M_BICUBIC (the stretched kernel)
+    int strip;       // antialias taps: output pixels per block (at most the kernel's 128 P)
     size_t smem;
 };
 
@@ -156,6 +158,16 @@ int win_pixels(int C, int dtype, bool x2);
 bool win_is_x2(const Geom& g);
 bool win_config(const Geom& g, int method, int dtype, WinCfg& c, bool allow_x2 = true);
 cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, void* dst, WinCfg c, cudaStream_t st);
+// Antialiased resampling (RS_FLAG_ANTIALIAS) on the general window form:
+// the most taps any output has on either axis (antialias_taps), the tap
+// capacity K (4 or 8; 0: too many), configuration and launch (out_dtype /
+// no: the fused pre-process's normalised planar output when norm is set).
+int antialias_taps(const Geom& g, int method);
+bool win_config_aa(const Geom& g, int method, int dtype, int K, WinCfg& c);
+cudaError_t launch_win_aa(const Geom& g, int method, int dtype, const void* src, void* dst, int K, WinCfg c,
+                          cudaStream_t st);
+cudaError_t launch_win_aa_norm(const Geom& g, int method, int out_dtype, const void* src, void* dst, int K, WinCfg c,
+                               const NormOut& no, cudaStream_t st);
 // The fused pre-process on the window kernels: uint8 interleaved source
 // (g describes it; g.dp / g.dst_pitch the output images and rows),
 // normalised planar output of out_dtype (DT_F16, DT_BF16 or DT_F32).

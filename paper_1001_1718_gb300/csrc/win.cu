@@ -146,6 +146,55 @@ bool win_config(const Geom& g, int method, int dtype, WinCfg& c, bool allow_x2)
     return c.smem <= max_smem_per_block();
 }
 
+// The most antialias taps an output has on axis n -> m (the integer bounds
+// the kernels use).
+static int aa_axis_taps(int n, int m, int method)
+{
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        int lo, hi;
+        aa_range(j, n, m, method, lo, hi);
+        k = std::max(k, hi - lo);
+    }
+    return k;
+}
+
+int antialias_taps(const Geom& g, int method)
+{
+    return std::max(aa_axis_taps(g.H, g.Ho, method), aa_axis_taps(g.W, g.Wo, method));
+}
+
+bool win_config_aa(const Geom& g, int method, int dtype, int K, WinCfg& c)
+{
+    if ((method != M_BILINEAR && method != M_BICUBIC) || (K != 4 && K != 8)) return false;
+    if (g.C < 1 || g.C > 4) return false;
+    if (c.chunk < K || c.chunk % K || c.chunk > 32) return false;
+    const int es = (int)dtype_size(dtype);
+    const int P0 = win_pixels(g.C, dtype, false);
+    const int P = K > 4 ? std::max(2, P0 / 2) : P0;
+    const int SP = kWinThreads * P;
+    c.band_cap = std::min(kWinMaxBand, g.Ho);
+    if ((int64_t)c.band_cap * g.dst_pitch >= (int64_t)INT32_MAX) return false;
+    c.pos_cap = (int)(((int64_t)(c.band_cap - 1) * g.H + g.Ho - 1) / g.Ho) + 2;
+    c.aa_method = method;
+    // The widest strip (128 P pixels, halved down to one warp's 32) whose
+    // footprint fits in shared memory.
+    for (int strip = std::min(SP, std::max(32, (g.Wo + 31) & ~31)); strip >= 32; strip /= 2) {
+        // first taps advance by at most ceil(n / m) + 1 per output
+        const int span_px = (int)(((int64_t)(strip - 1) * g.W + g.Wo - 1) / g.Wo) + 1 + K;
+        const int per = (span_px * g.C * es + 15) / 16 + 1;
+        c.strip = strip;
+        c.swe = g.C * ((span_px + 3) & ~3);
+        c.raw_row = per * 16;
+        c.tab_off = (int)align16(sizeof(float) * (size_t)c.chunk * c.swe);
+        const size_t tabs = sizeof(float2) * (size_t)c.band_cap * K + sizeof(int) * ((size_t)c.band_cap + c.pos_cap);
+        c.raw_off = (int)align16((size_t)c.tab_off + tabs);
+        c.smem = (size_t)c.raw_off + 2 * (size_t)c.chunk * c.raw_row;
+        if (c.smem <= max_smem_per_block()) return true;
+    }
+    return false;
+}
+
 cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, void* dst, WinCfg c, cudaStream_t st)
 {
     const bool x2 = win_is_x2(g);

@@ -276,18 +276,34 @@ __device__ __forceinline__ void win_store_px(T* p, const float (&x)[C], bool vec
 
 // General form, the work of one block: strip bx and band by of one plane
 // (s, d point at the plane). Used by the single-image kernel and the batch's
-// persistent window kernels.
-template <int KT, int C, typename T, typename TO = T, bool NORM = false>
+// persistent window kernels. TM = TAP_POINT: the taps of Eqs. 1-5 (KT = 2
+// bilinear, 4 bicubic); TM = TAP_AA: the antialias taps (RS_FLAG_ANTIALIAS:
+// the kernel of cfg.aa_method stretched by the downscale factor, at most KT
+// per axis, renormalised), with half the pixels per lane at KT = 8.
+enum { TAP_POINT = 0, TAP_AA = 1 };
+
+template <int C, typename T, int TM, int KT>
+struct WinGen {
+    static constexpr int P0 = WinShape<C, T, false>::P;
+    static constexpr int P = (TM == TAP_AA && KT > 4) ? (P0 / 2 < 2 ? 2 : P0 / 2) : P0;
+    static constexpr int SP = kWinThreads * P;
+};
+
+template <int KT, int C, typename T, typename TO = T, bool NORM = false, int TM = TAP_POINT>
 __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s, TO* __restrict__ d, const WinCfg& cfg,
                                          int bx, int by, float* sm, unsigned int* fault, const NormOut& no = NormOut{})
 {
-    using S = WinShape<C, T, false>;
-    constexpr int P = S::P, NP = S::NP, NT = kWinThreads;
+    using S = WinGen<C, T, TM, KT>;
+    constexpr int P = S::P, NP = P / 2, NT = kWinThreads;
     constexpr int ES = (int)sizeof(T);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    const int j_lo = bx * S::SP;                     // first pixel of the strip
-    const int j_hi = min(g.Wo, j_lo + S::SP) - 1;    // last pixel of the strip
+    // Strip of output pixels: 128 P, or for antialias taps cfg.strip <= 128 P
+    // (a narrower strip keeps a large downscale's footprint in shared memory;
+    // the lanes past it idle in the arithmetic and still stage rows).
+    const int sw_px = TM == TAP_AA ? cfg.strip : S::SP;
+    const int j_lo = bx * sw_px;                     // first pixel of the strip
+    const int j_hi = min(g.Wo, j_lo + sw_px) - 1;    // last pixel of the strip
     const int yb = by * cfg.band_h;
     const int ye = min(g.Ho, yb + cfg.band_h);
     const int nrows = ye - yb;
@@ -296,8 +312,17 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
     // raw copy of a row starts at element base = px_lo C; staged rows are
     // channel-planar (plane c, position x = pixel px_lo + x), cfg.swe floats
     // per row.
-    const int px_lo = first_tap<KT>(j_lo, g.W, g.Wo, g.coord);
-    const int px_hi = first_tap<KT>(j_hi, g.W, g.Wo, g.coord) + KT - 1;
+    auto first_col = [&](int j) {
+        if constexpr (TM == TAP_AA) {
+            int lo, hi;
+            aa_range(j, g.W, g.Wo, cfg.aa_method, lo, hi);
+            return lo;
+        } else {
+            return first_tap<KT>(j, g.W, g.Wo, g.coord);
+        }
+    };
+    const int px_lo = first_col(j_lo);
+    const int px_hi = first_col(j_hi) + KT - 1;
     const int npx = px_hi - px_lo + 1;
     const int base = px_lo * C;
     const int span = npx * C;
@@ -320,7 +345,8 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
     // Positions of the band: source rows b_first .. b_last are first taps.
     for (int i = tid; i < nrows; i += NT) {
         float w[KT];
-        RF[i] = taps<KT>(yb + i, g.H, g.Ho, g.coord, g.a, w);
+        if constexpr (TM == TAP_AA) aa_taps<KT>(yb + i, g.H, g.Ho, cfg.aa_method, g.a, RF[i], w, fault);
+        else RF[i] = taps<KT>(yb + i, g.H, g.Ho, g.coord, g.a, w);
         #pragma unroll
         for (int q = 0; q < KT; ++q) RW[i * KT + q] = make_float2(w[q], w[q]);
     }
@@ -355,7 +381,13 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
             float* w = h ? w1 : w0;
             valid[m] = j <= j_hi;
             if (valid[m]) {
-                off[m] = taps<KT>(j, g.W, g.Wo, g.coord, g.a, w) - px_lo;
+                if constexpr (TM == TAP_AA) {
+                    int lo;
+                    aa_taps<KT>(j, g.W, g.Wo, cfg.aa_method, g.a, lo, w, fault);
+                    off[m] = lo - px_lo;
+                } else {
+                    off[m] = taps<KT>(j, g.W, g.Wo, g.coord, g.a, w) - px_lo;
+                }
             } else {
                 off[m] = 0;
                 #pragma unroll

@@ -130,14 +130,12 @@ def test_layout_validation(L):
     hwc5 = L.rs_layout_hwc(1, 8, 8, 5)
     assert L.rs_resize_ex(P, ctypes.byref(hwc5), Q, ctypes.byref(L.rs_layout_hwc(1, 4, 4, 5)),
                           B.RS_U8, 1, None, None) == B.RS_ERR_UNSUPPORTED
-    # unknown option flags; antialias is FP32 only and has no nearest form
+    # unknown option flags; antialias has no nearest form
     o = B.options()
     o.flags = 2
     assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_F32, B.RS_BILINEAR,
                           ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
     o.flags = B.RS_FLAG_ANTIALIAS
-    assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_U8, B.RS_BILINEAR,
-                          ctypes.byref(o), None) == B.RS_ERR_UNSUPPORTED
     assert L.rs_resize_ex(P, ctypes.byref(good_in), Q, ctypes.byref(good_out), B.RS_F32, B.RS_NEAREST,
                           ctypes.byref(o), None) == B.RS_ERR_INVALID_ARG
     # window chunks must hold whole groups of taps (4 for bicubic)
@@ -245,6 +243,9 @@ def test_resize_normalize_validation(L):
     assert call(outl=L.rs_layout_nchw(1, 3, 32, 32)) == B.RS_ERR_INVALID_ARG  # N differs
     assert call(opt=B.options(impl=B.RS_IMPL_TILED)) == B.RS_ERR_INVALID_ARG
     o = B.options()
-    o.flags = B.RS_FLAG_ANTIALIAS
+    o.flags = 2                                                   # an unknown flag
+    assert call(opt=o) == B.RS_ERR_INVALID_ARG
+    o = B.options(tile_h=8)
+    o.flags = B.RS_FLAG_ANTIALIAS                                 # the antialiased form takes no chunk height
     assert call(opt=o) == B.RS_ERR_INVALID_ARG
     assert call(dst=Q + 1) == B.RS_ERR_ALIGNMENT                  # FP16 output on an odd address

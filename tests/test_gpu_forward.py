@@ -471,11 +471,55 @@ def test_antialias_matches_oracle(rs, oracle, method):
     assert rs.debug_fault() == 0
 
 
+def _aa_taps(n, m, method):
+    """The most antialias taps an output of the axis n -> m has, by the
+    header's integer bounds: floor(((2j+1) n -+ 2 R F + m) / (2m)), F = max(n, m),
+    cut to [0, n)."""
+    R, F = (1 if method == BL else 2), max(n, m)
+    best = 0
+    for j in range(m):
+        a = (2 * j + 1) * n + m
+        lo, hi = max((a - 2 * R * F) // (2 * m), 0), min((a + 2 * R * F) // (2 * m), n)
+        best = max(best, hi - lo)
+    return best
+
+
+@pytest.mark.parametrize("method", [BL, BC])
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16", "f32"])
+def test_antialias_window_every_dtype(rs, oracle, method, dtype):
+    """RS_FLAG_ANTIALIAS on the general window form (antialias taps, at most 8
+    per axis) for every storage dtype: uint8 / FP16 / BF16 sources (and FP32
+    through impl='window'), interleaved and planar, down- and upscales,
+    ragged strips, against the FP64 definition under the storage rule."""
+    impl = "window" if dtype == "f32" else "auto"
+    cases = [((180, 240, 3), (90, 120)), ((97, 133, 3), (49, 67)), ((300, 520, 1), (170, 300)),
+             ((40, 36, 4), (90, 72)), ((256, 200, 3), (64, 52)), ((77, 91, 2), (77, 91))]
+    for k, (shape, (Ho, Wo)) in enumerate(cases):
+        H, W = shape[0], shape[1]
+        taps = max(_aa_taps(n, m, method) for n, m in ((H, Ho), (W, Wo)))
+        t, x64 = _src(1600 + k, shape, dtype)
+        if taps > 8:
+            with pytest.raises(rs.ResampleError):
+                rs.resize(t.cuda(), (Ho, Wo), MNAME[method], antialias=True, impl=impl)
+            continue
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], antialias=True, impl=impl)
+        torch.cuda.synchronize()
+        check(y, oracle.resize_aa(x64, Ho, Wo, method), dtype, method, float(np.abs(x64).max()),
+              f"antialias window {dtype} {MNAME[method]} {shape}->{Ho}x{Wo}")
+    # planar (NCHW) planes
+    t, x64 = _src(1700, (2, 3, 120, 150), dtype)
+    y = rs.resize(t.cuda(), (60, 75), MNAME[method], layout="nchw", antialias=True, impl=impl)
+    torch.cuda.synchronize()
+    check(y, oracle.resize_aa_nchw(x64, 60, 75, method), dtype, method, float(np.abs(x64).max()),
+          f"antialias window nchw {dtype} {MNAME[method]}")
+    assert rs.debug_fault() == 0
+
+
 def test_antialias_refusals(rs):
     xf = torch.randn(64, 64, device="cuda")
     with pytest.raises(rs.ResampleError):          # more than 8 taps: bicubic below 1/2
         rs.resize(xf, (20, 20), "bicubic", antialias=True)
     with pytest.raises(rs.ResampleError):          # nearest has no filter to stretch
         rs.resize(xf, (32, 32), "nearest", antialias=True)
-    with pytest.raises(rs.ResampleError):          # FP32 only
-        rs.resize(torch.zeros(64, 64, dtype=torch.uint8, device="cuda"), (32, 32), "bilinear", antialias=True)
+    with pytest.raises(rs.ResampleError):          # more than 8 taps, uint8 too
+        rs.resize(torch.zeros(64, 64, dtype=torch.uint8, device="cuda"), (12, 12), "bilinear", antialias=True)

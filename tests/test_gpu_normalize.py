@@ -90,3 +90,26 @@ def test_resize_normalize_refusals(rs):
         rs.resize_normalize(x.float(), (16, 16), "bilinear", MEAN[:3], STD[:3])
     with pytest.raises(ValueError):
         rs.resize_normalize(x, (16, 16), "bilinear", MEAN[:2], STD[:2])
+
+
+@pytest.mark.parametrize("method", [BL, BC])
+def test_resize_normalize_antialias(rs, oracle, method):
+    """The fused pre-process with RS_FLAG_ANTIALIAS: serving-style
+    downscales of uint8 frames through the antialiased window form, against
+    the FP64 antialias definition followed by the normalisation."""
+    for k, (shape, (Ho, Wo)) in enumerate([((2, 240, 320, 3), (120, 160)), ((1, 300, 410, 3), (96, 131)),
+                                            ((3, 100, 90, 1), (100, 90))]):
+        img = _img(500 + k, shape)
+        x = torch.from_numpy(img).cuda()
+        C = shape[-1]
+        try:
+            y = rs.resize_normalize(x, (Ho, Wo), MNAME[method], MEAN[:C], STD[:C], dtype=torch.float16,
+                                    antialias=True)
+        except rs.ResampleError:
+            assert method == BC and shape[1] / Ho > 2   # more than 8 bicubic taps
+            continue
+        torch.cuda.synchronize()
+        ref = np.stack([((oracle.resize_aa(im.astype(np.float64), Ho, Wo, method) - np.array(MEAN[:C])) /
+                         np.array(STD[:C])).transpose(2, 0, 1) for im in img])
+        check(y, ref, "f16", method, 255.0 / min(STD[:C]), f"normalize antialias {MNAME[method]} {shape}->{Ho}x{Wo}")
+    assert rs.debug_fault() == 0
