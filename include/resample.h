@@ -67,16 +67,27 @@ typedef enum { RS_COORD_ASYMMETRIC = 0, RS_COORD_HALF_PIXEL = 1, RS_COORD_ALIGN_
  * AUTO   = the tuned (or default) kernel for the problem: GATHER for
  *          RS_NEAREST; for bilinear / bicubic REDUCE on RS_F32 vertical
  *          downscales to at least 1/4 (outputs >= 2^20 elements), WINDOW on
- *          large vertical upscales and uint8 outputs, where its footprint
- *          fits in shared memory; else STREAM, else TILED.
- * WINDOW = bilinear / bicubic: each thread owns 4 output elements (strided
- *          by 256) of a 1024-element strip for a whole band of rows and keeps the
- *          horizontally interpolated source rows its taps need in registers,
- *          so each output row is blended without touching shared memory;
- *          source rows are staged in chunks of tile_h rows (a multiple of
- *          the taps: 2 bilinear, 4 bicubic; double buffered, the next two
- *          chunks' copies in flight); waves = blocks per resident block slot
- *          (sets the band height).
+ *          vertical upscales and uint8 outputs of at least 2^22 elements,
+ *          where its footprint fits in shared memory; else STREAM, else
+ *          TILED. rs_autotune replaces this choice for a problem it has
+ *          timed.
+ * WINDOW = bilinear / bicubic, blocks of 128 threads, one per (strip of
+ *          output pixels, band of output rows, plane). Source rows are
+ *          copied with 16-byte cp.async in chunks of tile_h rows (a
+ *          multiple of the taps: 2 bilinear, 4 bicubic) two chunks ahead;
+ *          each thread interpolates every source row its pixels' taps reach
+ *          horizontally once, keeps the last 2 or 4 such rows in registers,
+ *          and blends each output row from them (no shared-memory traffic
+ *          per output row). Two forms:
+ *          exact x2 (asymmetric map, both axes exactly doubled): a thread
+ *          owns P consecutive output pixels (P * C * size >= 8 bytes where
+ *          the row allows), reads its footprint straight from the copied
+ *          bytes and stores its run with packed 4- to 16-byte stores; the
+ *          even outputs are copies, the odd ones the midpoint weights;
+ *          general ratios: a thread owns P pixels 32 apart (strips of
+ *          128 P pixels, P = 2 to 8 by channels and dtype) over source rows
+ *          converted to channel-planar FP32 in shared memory.
+ *          waves = blocks per resident block slot (sets the band height).
  * STREAM = one block per (column strip, band of rows), walking down the band
  *          in chunks; every source row is staged and horizontally
  *          interpolated once per strip; loads of the next chunk are issued
@@ -122,11 +133,17 @@ typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_S
  *   c = (j + 1/2) n / m, taps i = floor(c - R f + 1/2) .. floor(c + R f +
  *   1/2) - 1 (R = 1 bilinear, 2 bicubic) cut to [0, n), weights
  *   K((i + 1/2 - c) / f) renormalised to sum 1 (no edge replication; the
- *   coord option does not apply). RS_F32 only, at most 8 taps per axis
- *   (bilinear down to 1/4, bicubic down to 1/2), 16-byte source rows; one
- *   fused pass (the register-window kernel with computed taps).
- *   RS_ERR_UNSUPPORTED / RS_ERR_INVALID_ARG otherwise. Not for rs_resize,
- *   the batch or the backward. */
+ *   coord option does not apply). Every storage dtype, any downscale whose
+ *   tile footprint fits in shared memory (about 1/64 and above). Kernels:
+ *   RS_F32 with 16-byte source rows and at most 8 taps per axis: REDUCE's
+ *   fused pass with these taps; otherwise, up to 8 taps per axis (bilinear
+ *   down to 1/4, bicubic to 1/2), WINDOW's general form with these taps
+ *   (impl RS_IMPL_WINDOW selects it and refuses more taps); beyond that,
+ *   or with impl RS_IMPL_TILED, a tiled kernel that holds any number of
+ *   taps (tiles of 32 output columns: the tile's footprint rows are
+ *   interpolated horizontally into shared memory, then blended).
+ *   RS_NEAREST: RS_ERR_INVALID_ARG. Also for rs_resize_normalize and
+ *   rs_resize_backward (the adjoint of this map); not for the batch. */
 #define RS_FLAG_ANTIALIAS 1
 
 typedef struct {
@@ -178,7 +195,8 @@ rs_status rs_debug_fault(void* stream, uint32_t* code);
 /*
  * Resize one tightly packed HWC image (Sec. II.B, Eqs. 1-5): src is H x W x C
  * of `dtype`, dst is Ho x Wo x C of the same dtype, 1 <= C <= 4. Asymmetric
- * map (Eq. 1), a = -1/2, tiled kernel.
+ * map (Eq. 1), a = -1/2: rs_resize_ex with the default options, so the
+ * kernel is RS_IMPL_AUTO's choice.
  */
 rs_status rs_resize(const void* src, int H, int W, int C, rs_dtype dtype,
                     void* dst, int Ho, int Wo, rs_method method, void* stream);
@@ -204,9 +222,12 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
  * multiply-add per element with scale 1 / stddev[c] and bias -mean[c] /
  * stddev[c]. mean, stddev: C host floats each (finite, stddev nonzero). Options: coord and
  * cubic_a as for rs_resize_ex; impl RS_IMPL_AUTO or RS_IMPL_WINDOW (the
- * register-window kernel; tile_h = staged rows per chunk, waves); flags 0.
- * RS_NEAREST returns RS_ERR_UNSUPPORTED, and so does a downscale whose
- * staged footprint exceeds shared memory (about 1/5 and below).
+ * register-window kernel; tile_h = staged rows per chunk, waves); flags 0
+ * or RS_FLAG_ANTIALIAS (the antialiased window form up to 8 taps per axis,
+ * the many-tap tiled kernel beyond unless impl is RS_IMPL_WINDOW; tile_h
+ * must be 0). RS_NEAREST returns RS_ERR_UNSUPPORTED, and so does a point-
+ * sampled downscale whose staged footprint exceeds shared memory (about
+ * 1/5 and below; RS_FLAG_ANTIALIAS is the filter for such downscales).
  */
 rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, const rs_layout* out,
                               rs_dtype out_dtype, rs_method method, const float* mean, const float* stddev,
@@ -232,7 +253,11 @@ rs_status rs_resize_normalize(const void* src, const rs_layout* in, void* dst, c
  *   RS_IMPL_STREAM - two passes through the intermediate (x, then y);
  *   RS_IMPL_TILED  - one tiled pass through shared memory.
  * Only the tables (and, for STREAM, the intermediate) of the workspace are
- * used.
+ * used. opt->flags: 0, or RS_FLAG_ANTIALIAS for the adjoint of the
+ * antialiased forward (bilinear / bicubic; the tables then hold the
+ * transposed antialias weights, and the same three kernels apply); pass the
+ * same opt to rs_resize_backward_workspace. Other flags, and
+ * RS_FLAG_ANTIALIAS with RS_NEAREST: RS_ERR_INVALID_ARG.
  */
 rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in,
                                        rs_method method, const rs_options* opt,

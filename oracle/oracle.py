@@ -251,6 +251,15 @@ def resize_aa_nchw(x, Ho: int, Wo: int, method: int, a: float = -0.5) -> np.ndar
     return np.einsum("ih,nchw,jw->ncij", Ay, x, Ax, optimize=True)
 
 
+def adjoint_aa_nchw(gy, H: int, W: int, method: int, a: float = -0.5) -> np.ndarray:
+    """Transpose of resize_aa_nchw(): dX = Ay^T dY Ax per plane, from the same
+    FP64 axis matrices; (N, C, H, W)."""
+    N, C, Ho, Wo = gy.shape
+    Ay = aa_axis_matrix(H, Ho, method, a)
+    Ax = aa_axis_matrix(W, Wo, method, a)
+    return np.einsum("ih,ncij,jw->nchw", Ay, np.asarray(gy, np.float64), Ax, optimize=True)
+
+
 def quantize_u8(v) -> np.ndarray:
     x = np.ascontiguousarray(v, np.float64)
     out = np.empty(x.shape, np.uint8)

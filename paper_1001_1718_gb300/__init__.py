@@ -147,7 +147,7 @@ def resize(x: torch.Tensor, size: Sequence[int], method="bilinear", *, layout: s
     "stream", "tiled", "plain" or "gather" (nearest only);
     tile = (tile_w, tile_h) and threads / waves override the kernel shape.
     antialias: stretch the bilinear / bicubic kernel by the downscale factor
-    (FP32 only; see RS_FLAG_ANTIALIAS in include/resample.h)."""
+    (see RS_FLAG_ANTIALIAS in include/resample.h)."""
     _require_cuda(x)
     Ho, Wo = int(size[0]), int(size[1])
     if out is None:
@@ -209,11 +209,13 @@ def resize_normalize(x: torch.Tensor, size: Sequence[int], method="bilinear", me
 
 
 def backward_workspace_bytes(grad_out: torch.Tensor, in_hw, method, *, layout="nchw",
-                             coord="asymmetric", cubic_a=-0.5) -> int:
+                             coord="asymmetric", cubic_a=-0.5, antialias: bool = False) -> int:
     H, W = int(in_hw[0]), int(in_hw[1])
     Lo = _layout(grad_out, layout)
     Li = _layout(torch.empty(_out_shape(grad_out, layout, H, W), dtype=grad_out.dtype, device="meta"), layout)
     o = _opts(coord, cubic_a, "auto", None, 0)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     n = ctypes.c_size_t(0)
     B.check(lib().rs_resize_backward_workspace(ctypes.byref(Lo), ctypes.byref(Li),
                                                _code(METHODS, method, "method"), ctypes.byref(o),
@@ -223,9 +225,11 @@ def backward_workspace_bytes(grad_out: torch.Tensor, in_hw, method, *, layout="n
 
 def resize_backward(grad_out: torch.Tensor, in_hw, method="bilinear", *, layout: str = "nchw",
                     coord="asymmetric", cubic_a: float = -0.5, grad_in: torch.Tensor | None = None,
-                    workspace: torch.Tensor | None = None, impl="auto") -> torch.Tensor:
+                    workspace: torch.Tensor | None = None, impl="auto",
+                    antialias: bool = False) -> torch.Tensor:
     """Adjoint of resize() for FP32: grad_in = A^T grad_out (deterministic).
-    impl="auto" runs the two-pass kernels, impl="tiled" the single-pass one."""
+    impl="auto" picks the kernel ("window", "stream": two passes, "tiled");
+    antialias=True is the adjoint of resize(..., antialias=True)."""
     _require_cuda(grad_out)
     H, W = int(in_hw[0]), int(in_hw[1])
     if grad_in is None:
@@ -233,6 +237,8 @@ def resize_backward(grad_out: torch.Tensor, in_hw, method="bilinear", *, layout:
                               device=grad_out.device)
     Lo, Li = _layout(grad_out, layout), _layout(grad_in, layout)
     o = _opts(coord, cubic_a, impl, None, 0)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     m = _code(METHODS, method, "method")
     n = ctypes.c_size_t(0)
     B.check(lib().rs_resize_backward_workspace(ctypes.byref(Lo), ctypes.byref(Li), m, ctypes.byref(o),
@@ -252,16 +258,18 @@ class ResizeFn(torch.autograd.Function):
     in the library's kernels)."""
 
     @staticmethod
-    def forward(ctx, x, size, method="bilinear", coord="asymmetric", cubic_a=-0.5):
+    def forward(ctx, x, size, method="bilinear", coord="asymmetric", cubic_a=-0.5, antialias=False):
         ctx.in_hw = (x.shape[-2], x.shape[-1])
-        ctx.cfg = (method, coord, cubic_a)
-        return resize(x.contiguous(), size, method, layout="nchw", coord=coord, cubic_a=cubic_a)
+        ctx.cfg = (method, coord, cubic_a, bool(antialias))
+        return resize(x.contiguous(), size, method, layout="nchw", coord=coord, cubic_a=cubic_a,
+                      antialias=bool(antialias))
 
     @staticmethod
     def backward(ctx, g):
-        method, coord, cubic_a = ctx.cfg
-        gi = resize_backward(g.contiguous(), ctx.in_hw, method, layout="nchw", coord=coord, cubic_a=cubic_a)
-        return gi, None, None, None, None
+        method, coord, cubic_a, antialias = ctx.cfg
+        gi = resize_backward(g.contiguous(), ctx.in_hw, method, layout="nchw", coord=coord, cubic_a=cubic_a,
+                             antialias=antialias)
+        return gi, None, None, None, None, None
 
 
 def _descs(srcs, dsts, methods) -> tuple:

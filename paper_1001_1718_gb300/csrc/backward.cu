@@ -81,6 +81,24 @@ static AxisRanges host_ranges(int n, int m, int method, int coord)
     return R;
 }
 
+// Antialias taps (method aa): outputs j with lo(j) <= i < hi(j).
+static AxisRanges host_ranges_aa(int n, int m, int aa)
+{
+    std::vector<int> lo(m), hi(m);
+    for (int j = 0; j < m; ++j) aa_range(j, n, m, aa, lo[j], hi[j]);
+    AxisRanges R;
+    R.lo.resize(n);
+    R.hi.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const int jl = (int)(std::upper_bound(hi.begin(), hi.end(), i) - hi.begin());
+        const int jh = (int)(std::upper_bound(lo.begin(), lo.end(), i) - lo.begin()) - 1;
+        R.lo[i] = jl;
+        R.hi[i] = jh;
+        R.kmax = std::max(R.kmax, jh - jl + 1);
+    }
+    return R;
+}
+
 __device__ __forceinline__ int first_tap_rt(int j, int n, int m, int method, int coord)
 {
     if (method == M_NEAREST) return first_tap<1>(j, n, m, coord);
@@ -109,7 +127,11 @@ struct TableAxis {
     float* w;
 };
 
-__global__ void k_adjoint_tables(TableAxis ya, TableAxis xa, int method, int coord, float a, unsigned int* fault)
+// aa != 0: the antialias taps of method aa (RS_FLAG_ANTIALIAS); their
+// ranges [lo(j), hi(j)) never decrease with j and lie inside the image, so
+// input i's outputs are those with hi(j) > i and lo(j) <= i.
+__global__ void k_adjoint_tables(TableAxis ya, TableAxis xa, int method, int coord, float a, int aa,
+                                 unsigned int* fault)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t ny = (int64_t)ya.n * ya.K;
@@ -118,6 +140,32 @@ __global__ void k_adjoint_tables(TableAxis ya, TableAxis xa, int method, int coo
     const int64_t u = t < ny ? t : t - ny;
     const int i = (int)(u / ax.K), k = (int)(u - (int64_t)i * ax.K);
     const int n = ax.n, m = ax.m;
+    if (aa) {
+        int l = 0, h = m, lo, hi;
+        while (l < h) {   // first j with hi(j) > i
+            const int mid = (l + h) >> 1;
+            aa_range(mid, n, m, aa, lo, hi);
+            if (hi > i) h = mid; else l = mid + 1;
+        }
+        const int jl = l;
+        h = m;
+        while (l < h) {   // first j with lo(j) > i
+            const int mid = (l + h) >> 1;
+            aa_range(mid, n, m, aa, lo, hi);
+            if (lo > i) h = mid; else l = mid + 1;
+        }
+        int cnt = max(0, l - jl);
+        if (cnt > ax.K) {
+            if (k == 0) report_fault(fault, FAULT_BWD_TAPS);
+            cnt = ax.K;
+        }
+        if (k == 0) {
+            ax.lo[i] = jl;
+            ax.cnt[i] = cnt;
+        }
+        ax.w[(int64_t)i * ax.K + k] = k < cnt ? aa_weight(jl + k, i, n, m, aa, a) : 0.0f;
+        return;
+    }
     const int KT = method == M_NEAREST ? 1 : method == M_BILINEAR ? 2 : 4;
     // jlo = first j with first(j) >= i - KT + 1 (0 for i == 0)
     int jl = 0;
@@ -611,11 +659,11 @@ struct BwdPlan {
 
 static constexpr size_t kAdjTBudget = (size_t)256 << 20;  // bytes of T per plane group
 
-static BwdPlan plan_tables(const Geom& g, int method)
+static BwdPlan plan_tables(const Geom& g, int method, int aa)
 {
     BwdPlan p;
-    p.ry = host_ranges(g.H, g.Ho, method, g.coord);
-    p.rx = host_ranges(g.W, g.Wo, method, g.coord);
+    p.ry = aa ? host_ranges_aa(g.H, g.Ho, aa) : host_ranges(g.H, g.Ho, method, g.coord);
+    p.rx = aa ? host_ranges_aa(g.W, g.Wo, aa) : host_ranges(g.W, g.Wo, method, g.coord);
     p.yK = std::max(1, p.ry.kmax);
     p.xK = std::max(1, p.rx.kmax);
     size_t o = 0;
@@ -798,7 +846,13 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
                            cudaStream_t st)
 {
     if (method != M_BILINEAR && method != M_BICUBIC) return RS_ERR_INVALID_ARG;
-    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW && o.impl != RS_IMPL_REDUCE) return RS_ERR_INVALID_ARG;
+    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW && o.impl != RS_IMPL_REDUCE && o.impl != RS_IMPL_TILED)
+        return RS_ERR_INVALID_ARG;
+    if (o.impl == RS_IMPL_TILED) {   // the many-tap tiled kernel on request
+        AaWideCfg wc;
+        if (!aa_wide_config(gf, method, wc)) return RS_ERR_UNSUPPORTED;
+        return cuda_status(launch_aa_wide(gf, dtype, src, dst, wc, st));
+    }
     if (dtype == DT_F32 && o.impl != RS_IMPL_WINDOW) {
         // FP32: the fused pass in its transposed roles reads the rows in place
         const Geom g = forward_as_adjoint(gf);
@@ -817,12 +871,18 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
         if (o.impl == RS_IMPL_REDUCE) return RS_ERR_UNSUPPORTED;
     }
     if (o.impl == RS_IMPL_REDUCE) return RS_ERR_UNSUPPORTED;
-    // any dtype: the general window form with antialias taps
+    // any dtype: the general window form with antialias taps (at most 8 per
+    // axis), else the many-tap tiled kernel
     int K = 0;
     WinCfg c;
-    if (!aa_window_setup(gf, method, dtype, K, c)) return RS_ERR_UNSUPPORTED;
-    c.waves = o.waves;
-    return cuda_status(launch_win_aa(gf, method, dtype, src, dst, K, c, st));
+    if (aa_window_setup(gf, method, dtype, K, c)) {
+        c.waves = o.waves;
+        return cuda_status(launch_win_aa(gf, method, dtype, src, dst, K, c, st));
+    }
+    if (o.impl == RS_IMPL_WINDOW) return RS_ERR_UNSUPPORTED;
+    AaWideCfg wc;
+    if (!aa_wide_config(gf, method, wc)) return RS_ERR_UNSUPPORTED;
+    return cuda_status(launch_aa_wide(gf, dtype, src, dst, wc, st));
 }
 
 rs_status resize_normalize_antialias(const Geom& g, int method, int out_dtype, const void* src, void* dst,
@@ -830,9 +890,14 @@ rs_status resize_normalize_antialias(const Geom& g, int method, int out_dtype, c
 {
     int K = 0;
     WinCfg c;
-    if (!aa_window_setup(g, method, DT_U8, K, c)) return RS_ERR_UNSUPPORTED;
-    c.waves = o.waves;
-    return cuda_status(launch_win_aa_norm(g, method, out_dtype, src, dst, K, c, no, st));
+    if (aa_window_setup(g, method, DT_U8, K, c)) {
+        c.waves = o.waves;
+        return cuda_status(launch_win_aa_norm(g, method, out_dtype, src, dst, K, c, no, st));
+    }
+    if (o.impl == RS_IMPL_WINDOW) return RS_ERR_UNSUPPORTED;
+    AaWideCfg wc;
+    if (!aa_wide_config(g, method, wc)) return RS_ERR_UNSUPPORTED;
+    return cuda_status(launch_aa_wide_norm(g, out_dtype, src, dst, wc, no, st));
 }
 
 // Host ranges of the point taps in the window pass's forward roles: rows
@@ -928,6 +993,19 @@ static rs_status bwd_geom(const rs_layout* out, const rs_layout* in, rs_method m
     return geom_from_layouts(in, out, RS_F32, method, o, g, li, lo);
 }
 
+// RS_FLAG_ANTIALIAS: the adjoint of the antialiased forward (bilinear or
+// bicubic); aa = the method whose stretched kernel gives the taps, else 0.
+static rs_status bwd_flags(const rs_options& o, rs_method method, int& aa)
+{
+    if (o.flags & ~RS_FLAG_ANTIALIAS) return RS_ERR_INVALID_ARG;
+    aa = 0;
+    if (o.flags & RS_FLAG_ANTIALIAS) {
+        if (method != RS_BILINEAR && method != RS_BICUBIC) return RS_ERR_INVALID_ARG;
+        aa = method == RS_BILINEAR ? M_BILINEAR : M_BICUBIC;
+    }
+    return RS_OK;
+}
+
 extern "C" {
 
 rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in, rs_method method,
@@ -935,10 +1013,13 @@ rs_status rs_resize_backward_workspace(const rs_layout* out, const rs_layout* in
 {
     if (!bytes) return RS_ERR_INVALID_ARG;
     const rs_options o = options_or_default(opt);
-    Geom g;
-    rs_status s = bwd_geom(out, in, method, o, g);
+    int aa = 0;
+    rs_status s = bwd_flags(o, method, aa);
     if (s != RS_OK) return s;
-    *bytes = plan_tables(g, method).ws_bytes;
+    Geom g;
+    s = bwd_geom(out, in, method, o, g);
+    if (s != RS_OK) return s;
+    *bytes = plan_tables(g, method, aa).ws_bytes;
     return RS_OK;
 }
 
@@ -948,12 +1029,14 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
 {
     if (dtype != RS_F32) return RS_ERR_UNSUPPORTED;
     const rs_options o = options_or_default(opt);
-    if (o.flags) return RS_ERR_INVALID_ARG;   // no antialiased backward
+    int aa = 0;
+    rs_status s = bwd_flags(o, method, aa);
+    if (s != RS_OK) return s;
     Geom g;
     // make_geom checks pointers, alignment and overlap with src = dX, dst = dY.
-    rs_status s = make_geom(grad_in, in, grad_out, out, RS_F32, method, o, g);
+    s = make_geom(grad_in, in, grad_out, out, RS_F32, method, o, g);
     if (s != RS_OK) return s;
-    BwdPlan p = plan_tables(g, method);
+    BwdPlan p = plan_tables(g, method, aa);
     if (!workspace || workspace_bytes < p.ws_bytes) return RS_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) % 256) return RS_ERR_ALIGNMENT;
     {
@@ -1005,7 +1088,7 @@ rs_status rs_resize_backward(const void* grad_out, const rs_layout* out, void* g
         const TableAxis ya{g.H, g.Ho, tb.yK, (int*)tb.ylo, (int*)tb.ycnt, (float*)tb.yw};
         const TableAxis xa{g.W, g.Wo, tb.xK, (int*)tb.xlo, (int*)tb.xcnt, (float*)tb.xw};
         const int64_t entries = (int64_t)g.H * tb.yK + (int64_t)g.W * tb.xK;
-        k_adjoint_tables<<<(unsigned)((entries + 127) / 128), 128, 0, st>>>(ya, xa, method, g.coord, g.a, fw);
+        k_adjoint_tables<<<(unsigned)((entries + 127) / 128), 128, 0, st>>>(ya, xa, method, g.coord, g.a, aa, fw);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);

@@ -203,6 +203,18 @@ __host__ __device__ inline void aa_range(int j, int n, int m, int method, int& l
     hi = (int)(h > n ? n : h);   // exclusive
 }
 
+// Unnormalised antialias weight of source index i for the output whose
+// centre is cj / (2 n) (cj = (2 j + 1) n): the kernel at the stretched
+// distance u = |(2 i + 1) m - cj| / (2 max(n, m)).
+__device__ __forceinline__ float aa_kernel(int i, int m, int64_t cj, float inv2F, int method, float a)
+{
+    const float u = fabsf((float)((int64_t)(2 * i + 1) * m - cj) * inv2F);
+    if (method == M_BILINEAR) return fmaxf(0.0f, 1.0f - u);
+    if (u <= 1.0f) return ((a + 2.0f) * u - (a + 3.0f)) * u * u + 1.0f;
+    if (u < 2.0f) return ((a * u - 5.0f * a) * u + 8.0f * a) * u - 4.0f * a;
+    return 0.0f;
+}
+
 template <int K>
 __device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a, int& lo, float* w,
                                         unsigned int* fault)
@@ -219,19 +231,30 @@ __device__ __forceinline__ void aa_taps(int j, int n, int m, int method, float a
     float tot = 0.0f;
     #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float v = 0.0f;
-        if (k < cnt) {
-            const float u = fabsf((float)((int64_t)(2 * (lo + k) + 1) * m - cj) * inv2F);
-            if (method == M_BILINEAR) v = fmaxf(0.0f, 1.0f - u);
-            else if (u <= 1.0f) v = ((a + 2.0f) * u - (a + 3.0f)) * u * u + 1.0f;
-            else if (u < 2.0f) v = ((a * u - 5.0f * a) * u + 8.0f * a) * u - 4.0f * a;
-        }
+        const float v = k < cnt ? aa_kernel(lo + k, m, cj, inv2F, method, a) : 0.0f;
         w[k] = v;
         tot += v;
     }
     const float inv = tot != 0.0f ? 1.0f / tot : 1.0f;
     #pragma unroll
     for (int k = 0; k < K; ++k) w[k] *= inv;
+}
+
+// The renormalised antialias weight of source index i in output j's taps
+// (0 outside them): the value aa_taps gives that tap, for any tap count.
+__device__ __forceinline__ float aa_weight(int j, int i, int n, int m, int method, float a)
+{
+    int lo, hi;
+    aa_range(j, n, m, method, lo, hi);
+    const float inv2F = 1.0f / (2.0f * (float)max(n, m));
+    const int64_t cj = (int64_t)(2 * j + 1) * n;
+    float tot = 0.0f, wi = 0.0f;
+    for (int t = lo; t < hi; ++t) {
+        const float v = aa_kernel(t, m, cj, inv2F, method, a);
+        tot += v;
+        if (t == i) wi = v;
+    }
+    return wi * (tot != 0.0f ? 1.0f / tot : 1.0f);
 }
 
 }  // namespace rs

@@ -112,6 +112,16 @@ struct WinCfg {
     size_t smem;
 };
 
+// Antialiased resampling with many taps per axis (aa_wide.cu): tiles of 32
+// output columns x TH rows; KX / KY = the most taps of an output along x /
+// y; fw / nr = the widest source span of a tile's columns / rows; RG =
+// source rows staged at a time; s_off = float offset of the staged rows in
+// shared memory (after the tap tables).
+struct AaWideCfg {
+    int KX, KY, TH, RG, fw, nr, method, s_off;
+    size_t smem;
+};
+
 // Output of the fused pre-process (rs_resize_normalize): planar channels,
 // channel c of an image at c * c_stride elements from its first element;
 // each value is the resampled FP32 value times scale[c] plus bias[c]
@@ -168,6 +178,12 @@ cudaError_t launch_win_aa(const Geom& g, int method, int dtype, const void* src,
                           cudaStream_t st);
 cudaError_t launch_win_aa_norm(const Geom& g, int method, int out_dtype, const void* src, void* dst, int K, WinCfg c,
                                const NormOut& no, cudaStream_t st);
+// Antialias taps beyond the window forms (aa_wide.cu): false where a
+// tile's footprint cannot fit in shared memory.
+bool aa_wide_config(const Geom& g, int method, AaWideCfg& c);
+cudaError_t launch_aa_wide(const Geom& g, int dtype, const void* src, void* dst, const AaWideCfg& c, cudaStream_t st);
+cudaError_t launch_aa_wide_norm(const Geom& g, int out_dtype, const void* src, void* dst, const AaWideCfg& c,
+                                const NormOut& no, cudaStream_t st);
 // The fused pre-process on the window kernels: uint8 interleaved source
 // (g describes it; g.dp / g.dst_pitch the output images and rows),
 // normalised planar output of out_dtype (DT_F16, DT_BF16 or DT_F32).

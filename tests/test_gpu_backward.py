@@ -198,3 +198,70 @@ def test_window_adjoint(rs, oracle, method, coord):
     with pytest.raises(rs.ResampleError):
         rs.resize_backward(torch.randn(1, 1, 40, 41, device="cuda"), (20, 20), "bilinear", impl="window")
     assert rs.debug_fault() == 0
+
+
+# ---------------------------------------------------------------------------
+# The adjoint of the antialiased forward (RS_FLAG_ANTIALIAS)
+
+def _tol_aa(oracle, H, W, Ho, Wo, method, gmax):
+    Ay = oracle.aa_axis_matrix(H, Ho, method)
+    Ax = oracle.aa_axis_matrix(W, Wo, method)
+    return 1e-5 * max(1.0, gmax) * np.abs(Ay.T).sum(1).max() * np.abs(Ax.T).sum(1).max()
+
+
+AA_SHAPES = [(64, 80, 32, 40), (97, 133, 41, 29), (50, 60, 75, 90), (33, 47, 8, 12), (300, 257, 120, 100),
+             (1, 40, 1, 13), (29, 1, 7, 1)]
+
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("impl", ["auto", "stream", "tiled"])
+def test_antialias_adjoint_matches_oracle(rs, oracle, method, impl):
+    r = np.random.default_rng(61 + method)
+    for (H, W, Ho, Wo) in AA_SHAPES:
+        g = r.standard_normal((2, 3, Ho, Wo)).astype(np.float32)
+        gi = rs.resize_backward(torch.from_numpy(g).cuda(), (H, W), MN[method], antialias=True, impl=impl)
+        torch.cuda.synchronize()
+        ref = oracle.adjoint_aa_nchw(g.astype(np.float64), H, W, method)
+        err = np.abs(gi.cpu().numpy() - ref).max()
+        tol = _tol_aa(oracle, H, W, Ho, Wo, method, np.abs(g).max())
+        assert err <= tol, f"{MN[method]} {impl} {H}x{W}<-{Ho}x{Wo}: {err} > {tol}"
+    assert rs.debug_fault() == 0
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_antialias_autograd_and_central_differences(rs, oracle, method):
+    """ResizeFn(antialias=True): the forward equals resize(antialias=True),
+    the gradient equals resize_backward(antialias=True) and FP64 central
+    differences (eps = 1e-6) of the oracle's antialiased forward."""
+    x = torch.randn(2, 3, 64, 64, device="cuda", requires_grad=True)
+    y = rs.ResizeFn.apply(x, (26, 32), MN[method], "asymmetric", -0.5, True)
+    assert torch.equal(y.detach(), rs.resize(x.detach(), (26, 32), MN[method], layout="nchw", antialias=True))
+    g = torch.randn_like(y)
+    y.backward(g)
+    assert torch.equal(x.grad, rs.resize_backward(g, (64, 64), MN[method], antialias=True))
+    r = np.random.default_rng(22)
+    x0 = r.standard_normal((64, 64))
+    gg = r.standard_normal((26, 32)).astype(np.float32)
+    gi = rs.resize_backward(torch.from_numpy(gg).cuda(), (64, 64), MN[method], layout="hwc",
+                            antialias=True).cpu().numpy()
+    g64 = gg.astype(np.float64)
+    for (i, j) in [(0, 0), (63, 63), (0, 31), (17, 5), (40, 62), (33, 33)]:
+        xp, xm = x0.copy(), x0.copy()
+        xp[i, j] += 1e-6
+        xm[i, j] -= 1e-6
+        fd = (np.sum(oracle.resize_aa(xp, 26, 32, method)[:, :, 0] * g64) -
+              np.sum(oracle.resize_aa(xm, 26, 32, method)[:, :, 0] * g64)) / 2e-6
+        assert abs(gi[i, j] - fd) < 1e-4 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_antialias_adjoint_full_size(rs, oracle, method):
+    """FP32 32x3x512x512 at x0.5: every element of the antialiased adjoint."""
+    from paper_1001_1718_gb300 import workloads
+    g = workloads.normal_nchw(77, 32, 3, 256, 256).astype(np.float32)
+    gi = rs.resize_backward(torch.from_numpy(g).cuda(), (512, 512), MN[method], antialias=True)
+    torch.cuda.synchronize()
+    ref = oracle.adjoint_aa_nchw(g.astype(np.float64), 512, 512, method)
+    tol = _tol_aa(oracle, 512, 512, 256, 256, method, np.abs(g).max())
+    assert np.abs(gi.cpu().numpy() - ref).max() <= tol
+    assert rs.debug_fault() == 0

@@ -95,21 +95,21 @@ def test_resize_normalize_refusals(rs):
 @pytest.mark.parametrize("method", [BL, BC])
 def test_resize_normalize_antialias(rs, oracle, method):
     """The fused pre-process with RS_FLAG_ANTIALIAS: serving-style
-    downscales of uint8 frames through the antialiased window form, against
-    the FP64 antialias definition followed by the normalisation."""
-    for k, (shape, (Ho, Wo)) in enumerate([((2, 240, 320, 3), (120, 160)), ((1, 300, 410, 3), (96, 131)),
-                                            ((3, 100, 90, 1), (100, 90))]):
+    downscales of uint8 frames (the antialiased window form up to 8 taps per
+    axis, the many-tap tiled kernel beyond: a 1280x720 frame to 160x90),
+    against the FP64 antialias definition followed by the normalisation."""
+    cases = [((2, 240, 320, 3), (120, 160), torch.float16), ((1, 300, 410, 3), (96, 131), torch.bfloat16),
+             ((3, 100, 90, 1), (100, 90), torch.float32), ((1, 720, 1280, 3), (90, 160), torch.float16),
+             ((2, 333, 250, 4), (41, 29), torch.float32)]
+    names = {torch.float16: "f16", torch.bfloat16: "bf16", torch.float32: "f32"}
+    for k, (shape, (Ho, Wo), dt) in enumerate(cases):
         img = _img(500 + k, shape)
         x = torch.from_numpy(img).cuda()
         C = shape[-1]
-        try:
-            y = rs.resize_normalize(x, (Ho, Wo), MNAME[method], MEAN[:C], STD[:C], dtype=torch.float16,
-                                    antialias=True)
-        except rs.ResampleError:
-            assert method == BC and shape[1] / Ho > 2   # more than 8 bicubic taps
-            continue
+        y = rs.resize_normalize(x, (Ho, Wo), MNAME[method], MEAN[:C], STD[:C], dtype=dt, antialias=True)
         torch.cuda.synchronize()
         ref = np.stack([((oracle.resize_aa(im.astype(np.float64), Ho, Wo, method) - np.array(MEAN[:C])) /
                          np.array(STD[:C])).transpose(2, 0, 1) for im in img])
-        check(y, ref, "f16", method, 255.0 / min(STD[:C]), f"normalize antialias {MNAME[method]} {shape}->{Ho}x{Wo}")
+        check(y, ref, names[dt], method, 255.0 / min(STD[:C]),
+              f"normalize antialias {MNAME[method]} {shape}->{Ho}x{Wo}")
     assert rs.debug_fault() == 0

@@ -45,6 +45,8 @@ PY_MUTANTS = {
                                    "out[n] = ((y - m) * (1.0 / s[0])).transpose(2, 0, 1)"),
     "normalize_planar_axes": ("out[n] = ((y - m) / s).transpose(2, 0, 1)",
                               "out[n] = ((y - m) / s).transpose(2, 1, 0).reshape(C, Ho, Wo)"),
+    "aa_adjoint_axes_swapped": ('return np.einsum("ih,ncij,jw->nchw", Ay, np.asarray(gy, np.float64), Ax, optimize=True)',
+                                'return np.einsum("ih,ncij,jw->nchw", Ay, np.asarray(gy, np.float64), Ax[::-1], optimize=True)'),
 }
 
 

@@ -425,6 +425,35 @@ def test_aa_matches_torch_antialias(oracle, method, shape):
     assert np.abs(ref - t).max() < 1e-12
 
 
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("shape", [(64, 80, 32, 40), (50, 70, 19, 31), (20, 30, 45, 41)])
+def test_aa_adjoint_matches_torch_autograd(oracle, method, shape):
+    """The adjoint of the antialiased resampling against torch's own
+    backward of its antialiased interpolate (FP64 autograd)."""
+    torch = pytest.importorskip("torch")
+    H, W, Ho, Wo = shape
+    r = np.random.default_rng(H + 7 * W)
+    x = torch.from_numpy(r.standard_normal((2, 3, H, W))).requires_grad_(True)
+    gy = r.standard_normal((2, 3, Ho, Wo))
+    y = torch.nn.functional.interpolate(x, size=(Ho, Wo), mode={1: "bilinear", 2: "bicubic"}[method],
+                                        antialias=True, align_corners=False)
+    (y * torch.from_numpy(gy)).sum().backward()
+    ref = oracle.adjoint_aa_nchw(gy, H, W, method, -0.5)
+    assert np.abs(ref - x.grad.numpy()).max() < 1e-12
+
+
+def test_aa_adjoint_inner_product(oracle):
+    """<A x, g> = <x, A^T g> for a non-square downscale (A and A^T from the
+    forward and the adjoint separately)."""
+    r = np.random.default_rng(5)
+    x = r.standard_normal((1, 2, 41, 67))
+    g = r.standard_normal((1, 2, 13, 29))
+    for method in (1, 2):
+        lhs = np.sum(oracle.resize_aa_nchw(x, 13, 29, method) * g)
+        rhs = np.sum(x * oracle.adjoint_aa_nchw(g, 41, 67, method))
+        assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+
+
 def test_aa_rows_sum_to_one_and_closed_form(oracle):
     for n, m in ((100, 50), (97, 31), (30, 90), (64, 63)):
         for method in (1, 2):
