@@ -142,8 +142,8 @@ typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_S
  *   or with impl RS_IMPL_TILED, a tiled kernel that holds any number of
  *   taps (tiles of 32 output columns: the tile's footprint rows are
  *   interpolated horizontally into shared memory, then blended).
- *   RS_NEAREST: RS_ERR_INVALID_ARG. Also for rs_resize_normalize and
- *   rs_resize_backward (the adjoint of this map); not for the batch. */
+ *   RS_NEAREST: RS_ERR_INVALID_ARG. Also for rs_resize_normalize,
+ *   rs_resize_backward (the adjoint of this map) and the batch. */
 #define RS_FLAG_ANTIALIAS 1
 
 typedef struct {
@@ -296,6 +296,11 @@ typedef struct {
  * impl = RS_IMPL_TILED: every image as tiles of tile_w elements (0 = 512)
  *   x at most tile_h rows (0 = 32) with `threads` threads (0 = 256).
  * Other impl values return RS_ERR_INVALID_ARG.
+ * flags = RS_FLAG_ANTIALIAS: every image with the antialias taps (bilinear
+ *   / bicubic only; a nearest image returns RS_ERR_INVALID_ARG): window
+ *   items up to 8 taps per axis, the many-tap tiled kernel's tiles beyond
+ *   (and for every image under RS_IMPL_TILED). Other flags:
+ *   RS_ERR_INVALID_ARG.
  */
 
 /* Device workspace bytes rs_resize_batched needs for these descriptors. */
@@ -318,7 +323,7 @@ rs_status rs_resize_batched(const rs_image_desc* d, int n, rs_dtype dtype,
  *
  * The work list goes into a fixed array of device memory declared inside
  * the library (static __device__, RS_NOALLOC_MAX_IMAGES descriptors, about
- * 480 KB); every GPU that loads the library holds it until the process
+ * 650 KB); every GPU that loads the library holds it until the process
  * exits. Nothing is allocated: no cudaMalloc, cudaFree or allocating library
  * routine is called.
  *   - n > RS_NOALLOC_MAX_IMAGES returns RS_ERR_WORKSPACE, before any work.

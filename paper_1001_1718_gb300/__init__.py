@@ -299,10 +299,11 @@ def batched_workspace_bytes(srcs, dsts, methods) -> int:
 
 def resize_batched(srcs: Sequence[torch.Tensor], sizes, methods, *, coord="asymmetric",
                    cubic_a: float = -0.5, outs=None, workspace: torch.Tensor | None = None,
-                   impl: str = "auto", tile=None, threads: int = 0):
+                   impl: str = "auto", tile=None, threads: int = 0, antialias: bool = False):
     """Resample a ragged list of (H, W, C) images in one persistent launch.
     impl="window": tile = (band rows, chunk rows) of the window items;
-    impl="tiled": tile = (elements, rows) of every image's tiles."""
+    impl="tiled": tile = (elements, rows) of every image's tiles.
+    antialias=True: every image with the antialias taps (bilinear / bicubic)."""
     _require_cuda(*srcs)
     if outs is None:
         outs = [torch.empty((int(h), int(w), s.shape[2]), dtype=s.dtype, device=s.device)
@@ -314,6 +315,8 @@ def resize_batched(srcs: Sequence[torch.Tensor], sizes, methods, *, coord="asymm
     if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
     o = _opts(coord, cubic_a, impl, tile, threads)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     with _on_device(srcs[0]):
         B.check(lib().rs_resize_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),
                                         _stream(srcs[0])), "rs_resize_batched")
@@ -325,7 +328,7 @@ class BatchedPlan:
     captured as a CUDA graph) and replayed by launch()."""
 
     def __init__(self, srcs, outs, methods, *, coord="asymmetric", cubic_a: float = -0.5,
-                 impl: str = "auto", tile=None, threads: int = 0):
+                 impl: str = "auto", tile=None, threads: int = 0, antialias: bool = False):
         _require_cuda(*srcs, *outs)
         self.srcs, self.outs = list(srcs), list(outs)
         arr, n = _descs(self.srcs, self.outs, methods)
@@ -334,6 +337,8 @@ class BatchedPlan:
         B.check(lib().rs_resize_batched_workspace(arr, n, dt, ctypes.byref(nb)), "rs_resize_batched_workspace")
         self.workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
         o = _opts(coord, cubic_a, impl, tile, threads)
+        if antialias:
+            o.flags = B.RS_FLAG_ANTIALIAS
         self._plan = ctypes.c_void_p()
         self.device = srcs[0].device
         with torch.cuda.device(self.device):
@@ -384,7 +389,7 @@ def autotune(x: torch.Tensor, size, method, *, layout="hwc", coord="asymmetric",
 
 
 def autotune_batched(srcs, outs, methods, *, coord="asymmetric", cubic_a: float = -0.5,
-                     workspace: torch.Tensor | None = None) -> dict:
+                     workspace: torch.Tensor | None = None, antialias: bool = False) -> dict:
     """Time the batch at each item shape and cache the fastest for later
     batch calls on the same descriptors (the outputs are written)."""
     _require_cuda(*srcs, *outs)
@@ -395,6 +400,8 @@ def autotune_batched(srcs, outs, methods, *, coord="asymmetric", cubic_a: float 
     if workspace is None or workspace.numel() * workspace.element_size() < nb.value:
         workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=srcs[0].device)
     o = _opts(coord, cubic_a, "auto", None, 0)
+    if antialias:
+        o.flags = B.RS_FLAG_ANTIALIAS
     best = B.RsTileConfig()
     with _on_device(srcs[0]):
         B.check(lib().rs_autotune_batched(arr, n, dt, workspace.data_ptr(), nb.value, ctypes.byref(o),

@@ -15,7 +15,9 @@
 // blocks per SM); block b takes items b, b + gridDim.x, ..., finds each
 // item's image by binary search in the class prefix and runs the image's
 // per-block work. No block waits on another. The replayable plan records the
-// class launches as independent nodes of one CUDA graph.
+// class launches as independent nodes of one CUDA graph. With
+// RS_FLAG_ANTIALIAS every image is resampled with the antialias taps: window
+// items up to 8 taps per axis, many-tap tiles beyond.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -26,6 +28,7 @@
 #include "capi_internal.h"
 #include "win_body.cuh"
 #include "tile_body.cuh"
+#include "aa_wide.cuh"
 
 namespace rs {
 
@@ -34,16 +37,20 @@ struct BatchImage {
     void* dst;
     int64_t src_pitch, dst_pitch;
     int H, W, Ho, Wo;
-    int C, method, tiles_x, kind;          // tiles_x: items per row of items; kind 0 tile, 1 window
+    int C, method, tiles_x, kind;          // tiles_x: items per row of items; kind 0 tile, 1 window, 2 many-tap
     int tile_w, tile_h, sh_max, swe_max;   // kind 0: tiled-kernel tile
     int chunk, band_h, swe, raw_row, band_cap, pos_cap, tab_off, raw_off;   // kind 1: window config
+    int aa, strip;                         // antialias taps: the stretched method (0: point taps), window strip
+    int KX, KY, TH, RG, fw, nr, s_off, pad;   // kind 2: many-tap antialias tiles (AaWideCfg)
 };
 
 // Classes: 0..7 = window (KT 2 / 4) x (C 1..4) with a footprint of at most
 // kWindowSmallSmem bytes of shared memory (three blocks per SM), 8..15 the
 // same with larger footprints (up to ~100 KB, two blocks per SM), 16 =
 // tiled. Splitting by footprint keeps one large image from lowering the
-// occupancy of its whole class.
+// occupancy of its whole class. With RS_FLAG_ANTIALIAS (the whole batch)
+// the window classes hold antialias taps, at most K = 4 / 8 per axis in
+// place of KT = 2 / 4, and class 16 the many-tap antialias tiles.
 static constexpr int kClasses = 17;
 static constexpr int kTileClass = 16;
 static constexpr size_t kWindowSmallSmem = 72 * 1024;
@@ -73,8 +80,9 @@ __device__ __forceinline__ Geom image_geom(const BatchImage& im, int coord, floa
     return g;
 }
 
-// Window items of one (KT, C) class.
-template <int KT, int C, typename T>
+// Window items of one (KT, C) class: point taps (TM = TAP_POINT, KT = the
+// method's taps) or antialias taps (TM = TAP_AA, at most KT per axis).
+template <int KT, int C, typename T, int TM = TAP_POINT>
 __global__ void __launch_bounds__(kWinThreads, 2)
 k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start, int n, int64_t total,
                  int coord, float a, unsigned int* fault)
@@ -99,10 +107,45 @@ k_batched_window(const BatchImage* __restrict__ imgs, const int64_t* __restrict_
         wc.pos_cap = im.pos_cap;
         wc.tab_off = im.tab_off;
         wc.raw_off = im.raw_off;
+        wc.aa_method = im.aa;
+        wc.strip = im.strip;
         wc.smem = 0;
-        win_body<KT, C, T>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), wc,
-                                  (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
+        win_body<KT, C, T, T, false, TM>(g, static_cast<const T*>(im.src), static_cast<T*>(im.dst), wc,
+                                         (int)(local % im.tiles_x), (int)(local / im.tiles_x), sm, fault);
         __syncthreads();   // the next item reuses shared memory
+    }
+}
+
+// Many-tap antialias tiles (kind 2) of any channel count.
+template <typename T>
+__global__ void __launch_bounds__(kAwNT)
+k_batched_aa_wide(const BatchImage* __restrict__ imgs, const int64_t* __restrict__ start, int n, int64_t total,
+                  int coord, float a, unsigned int* fault)
+{
+    extern __shared__ __align__(16) float sm[];
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int k = find_image(start, n, t);
+        const BatchImage im = imgs[k];
+        const int64_t local = t - __ldg(start + k);
+        if (local < 0 || local >= __ldg(start + k + 1) - __ldg(start + k) || im.kind != 2) {
+            if (threadIdx.x == 0) report_fault(fault, FAULT_BATCH_INDEX);   // uniform over the block
+            continue;
+        }
+        const Geom g = image_geom(im, coord, a);
+        AaWideCfg c;
+        c.KX = im.KX; c.KY = im.KY; c.TH = im.TH; c.RG = im.RG;
+        c.fw = im.fw; c.nr = im.nr; c.method = im.aa; c.s_off = im.s_off;
+        c.smem = 0;
+        const T* s = static_cast<const T*>(im.src);
+        T* d = static_cast<T*>(im.dst);
+        const int bx = (int)(local % im.tiles_x), by = (int)(local / im.tiles_x);
+        switch (im.C) {
+        case 1: aa_wide_body<1, T, T, false>(g, s, d, c, bx, by, sm, fault, NormOut{}); break;
+        case 2: aa_wide_body<2, T, T, false>(g, s, d, c, bx, by, sm, fault, NormOut{}); break;
+        case 3: aa_wide_body<3, T, T, false>(g, s, d, c, bx, by, sm, fault, NormOut{}); break;
+        default: aa_wide_body<4, T, T, false>(g, s, d, c, bx, by, sm, fault, NormOut{}); break;
+        }
+        __syncthreads();   // the next tile reuses shared memory
     }
 }
 
@@ -183,6 +226,54 @@ struct BatchShape {
     int chunk, band;
 };
 
+// Antialias taps (RS_FLAG_ANTIALIAS): window items with at most K = 4 or 8
+// taps per axis, in the class of (K, C, footprint tier); else (more taps,
+// or every image when the batch is tiled) many-tap tiles in the tile class.
+static rs_status prepare_image_aa(const rs_image_desc& x, const Geom& g, int dtype, const BatchShape& sh,
+                                  BatchImage& im, int& cls, int64_t& items, size_t& smem)
+{
+    if (x.method != RS_BILINEAR && x.method != RS_BICUBIC) return RS_ERR_INVALID_ARG;
+    im.aa = x.method == RS_BILINEAR ? M_BILINEAR : M_BICUBIC;
+    const int k = antialias_taps(g, im.aa);
+    const int K = k <= 4 ? 4 : k <= 8 ? 8 : 0;
+    // chunks of 8 staged rows, else 4 (K = 4), else 16, within the
+    // small-footprint budget; else the same within ~100 KB
+    const int chunks[3] = {sh.chunk ? sh.chunk : 8, sh.chunk ? 0 : 4, sh.chunk ? 0 : 16};
+    for (int t = 0; K && !sh.tiled && t < 6; ++t) {
+        const int ch = chunks[t % 3];
+        if (!ch || ch % K) continue;
+        WinCfg wc{};
+        wc.chunk = ch;
+        if (!win_config_aa(g, im.aa, dtype, K, wc) || wc.smem > (t < 3 ? kWindowSmallSmem : 100 * 1024)) continue;
+        im.kind = 1;
+        im.chunk = wc.chunk;
+        const bool heavy = t >= 3 || x.Ho < x.H;
+        im.band_h = std::min(wc.band_cap, heavy ? std::min(sh.band, kHeavyBand) : sh.band);
+        im.swe = wc.swe;
+        im.band_cap = wc.band_cap;
+        im.pos_cap = wc.pos_cap;
+        im.tab_off = wc.tab_off;
+        im.raw_row = wc.raw_row;
+        im.raw_off = wc.raw_off;
+        im.strip = wc.strip;
+        im.tiles_x = (int)(((int64_t)x.Wo + wc.strip - 1) / wc.strip);
+        items = (int64_t)im.tiles_x * ((x.Ho + im.band_h - 1) / im.band_h);
+        smem = wc.smem;
+        cls = (wc.smem <= kWindowSmallSmem ? 0 : 8) + (K == 4 ? 0 : 4) + (x.C - 1);
+        return RS_OK;
+    }
+    AaWideCfg c;
+    if (!aa_wide_config(g, im.aa, c)) return RS_ERR_UNSUPPORTED;
+    im.kind = 2;
+    im.KX = c.KX; im.KY = c.KY; im.TH = c.TH; im.RG = c.RG;
+    im.fw = c.fw; im.nr = c.nr; im.s_off = c.s_off;
+    im.tiles_x = (x.Wo + 31) / 32;
+    items = (int64_t)im.tiles_x * ((x.Ho + c.TH - 1) / c.TH);
+    smem = c.smem;
+    cls = kTileClass;
+    return RS_OK;
+}
+
 // Validates one descriptor and fills its device descriptor: window items
 // (bilinear / bicubic, footprint within ~100 KB of shared memory) or tiles.
 // Returns the class, item count and shared-memory need.
@@ -207,6 +298,7 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
     im.src = x.src; im.dst = x.dst;
     im.src_pitch = x.src_pitch; im.dst_pitch = x.dst_pitch;
     im.H = x.H; im.W = x.W; im.Ho = x.Ho; im.Wo = x.Wo; im.C = x.C; im.method = x.method;
+    if (o.flags & RS_FLAG_ANTIALIAS) return prepare_image_aa(x, g, dtype, sh, im, cls, items, smem);
     if (x.method != RS_NEAREST && !sh.tiled) {
         // chunks of 8 rows, else 4, within the small-footprint budget; else
         // the same within ~100 KB (the large-footprint classes)
@@ -281,8 +373,8 @@ static std::string batch_key(const rs_image_desc* d, int n, int dtype, const rs_
         mix(d[k].method); mix(d[k].src_pitch); mix(d[k].dst_pitch);
     }
     char buf[96];
-    std::snprintf(buf, sizeof buf, ";sms=%d;batch;dt=%d;n=%d;coord=%d;h=%016llx", num_sms(), dtype, n, o.coord,
-                  (unsigned long long)h);
+    std::snprintf(buf, sizeof buf, ";sms=%d;batch;dt=%d;n=%d;coord=%d;aa=%d;h=%016llx", num_sms(), dtype, n, o.coord,
+                  (int)(o.flags & RS_FLAG_ANTIALIAS), (unsigned long long)h);
     return "gpu=" + device_tag() + buf;
 }
 
@@ -323,7 +415,7 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
     if (dtype < RS_U8 || dtype > RS_F32) return RS_ERR_INVALID_ARG;
     rs_status s = check_options(o, RS_BILINEAR);
     if (s != RS_OK) return s;
-    if (o.flags) return RS_ERR_INVALID_ARG;   // no antialiased batch
+    if (o.flags & ~RS_FLAG_ANTIALIAS) return RS_ERR_INVALID_ARG;
     BatchShape sh;
     if ((s = batch_shape(d, n, dtype, o, tuned, sh)) != RS_OK) return s;
     const bool window_opts = o.impl == RS_IMPL_WINDOW;   // tile_w / tile_h describe the window items
@@ -372,12 +464,31 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
     return RS_OK;
 }
 
-template <int KT, int C, typename T>
-static void* win_func() { return reinterpret_cast<void*>(&k_batched_window<KT, C, T>); }
+template <int KT, int C, typename T, int TM = TAP_POINT>
+static void* win_func() { return reinterpret_cast<void*>(&k_batched_window<KT, C, T, TM>); }
+
+// Antialias classes: (c & 4) ? 8 : 4 taps per axis, C = (c & 3) + 1; the
+// tile class holds the many-tap tiles.
+template <typename T>
+static void* class_func_aa(int c)
+{
+    if (c == kTileClass) return reinterpret_cast<void*>(&k_batched_aa_wide<T>);
+    switch (c & 7) {
+    case 0: return win_func<4, 1, T, TAP_AA>();
+    case 1: return win_func<4, 2, T, TAP_AA>();
+    case 2: return win_func<4, 3, T, TAP_AA>();
+    case 3: return win_func<4, 4, T, TAP_AA>();
+    case 4: return win_func<8, 1, T, TAP_AA>();
+    case 5: return win_func<8, 2, T, TAP_AA>();
+    case 6: return win_func<8, 3, T, TAP_AA>();
+    default: return win_func<8, 4, T, TAP_AA>();
+    }
+}
 
 template <typename T>
-static void* class_func_t(int c)
+static void* class_func_t(int c, bool aa)
 {
+    if (aa) return class_func_aa<T>(c);
     if (c == kTileClass) return reinterpret_cast<void*>(&k_batched<T>);
     switch (c & 7) {
     case 0: return win_func<2, 1, T>();
@@ -391,13 +502,13 @@ static void* class_func_t(int c)
     }
 }
 
-static void* class_func(int dtype, int c)
+static void* class_func(int dtype, int c, bool aa)
 {
     switch (dtype) {
-    case DT_U8: return class_func_t<uint8_t>(c);
-    case DT_F16: return class_func_t<__half>(c);
-    case DT_BF16: return class_func_t<__nv_bfloat16>(c);
-    default: return class_func_t<float>(c);
+    case DT_U8: return class_func_t<uint8_t>(c, aa);
+    case DT_F16: return class_func_t<__half>(c, aa);
+    case DT_BF16: return class_func_t<__nv_bfloat16>(c, aa);
+    default: return class_func_t<float>(c, aa);
     }
 }
 
@@ -423,8 +534,9 @@ static cudaError_t class_launches(const BatchLayout& L, int dtype, const rs_opti
     for (int c = 0; c < kClasses; ++c) {
         if (L.count[c] == 0 || L.total[c] == 0) continue;
         ClassLaunch& cl = out[nl++];
-        cl.func = class_func(dtype, c);
-        const int threads = c == kTileClass ? L.threads : kWinThreads;
+        const bool aa = (o.flags & RS_FLAG_ANTIALIAS) != 0;
+        cl.func = class_func(dtype, c, aa);
+        const int threads = c == kTileClass ? (aa ? kAwNT : L.threads) : kWinThreads;
         int per_sm = 0;
         cudaError_t e = prepare_kernel(cl.func, L.smem[c], threads, &per_sm);
         if (e != cudaSuccess) return e;

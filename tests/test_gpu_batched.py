@@ -158,3 +158,54 @@ def test_batch_item_shapes_agree(rs):
         rs.resize_batched(srcs, sizes, methods, impl="window", tile=(300, 8))
     rs.tune_cache_clear()
     assert rs.debug_fault() == 0
+
+
+def _aa_batch(seed, n, dtype):
+    """Ragged batch of mostly downscales (x0.08 to x1.6): items within the
+    window forms' 8 taps per axis and items beyond them (many-tap tiles)."""
+    from _parity import to_storage, as_f64
+    r = np.random.default_rng(seed)
+    srcs, sizes, methods, host = [], [], [], []
+    for k in range(n):
+        H, W = int(r.integers(20, 400)), int(r.integers(20, 400))
+        C = int(r.choice([1, 3, 4]))
+        s = float(r.uniform(0.08, 1.6))
+        Ho, Wo = max(1, int(H * s)), max(1, int(W * s * r.uniform(0.8, 1.25)))
+        x = r.integers(0, 256, (H, W, C)).astype(np.float64) if dtype == "u8" else r.standard_normal((H, W, C)) * 3
+        t = to_storage(x, dtype)
+        host.append(as_f64(t))
+        srcs.append(t.cuda())
+        sizes.append((Ho, Wo))
+        methods.append(MN[1 + k % 2])
+    return srcs, sizes, methods, host
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+def test_batched_antialias(rs, oracle, dtype):
+    """RS_FLAG_ANTIALIAS on the batch (window items and many-tap tiles in one
+    call), the replayable plan and the all-tiles shape, against the FP64
+    antialias definition under the storage rule; uint8 / FP16 items equal
+    the single-image antialiased call (the same kernels' arithmetic)."""
+    srcs, sizes, methods, host = _aa_batch(31, 20, dtype)
+    outs = rs.resize_batched(srcs, sizes, methods, antialias=True)
+    torch.cuda.synchronize()
+    for x, s, m, y, h in zip(srcs, sizes, methods, outs, host):
+        code = rs.METHODS[m]
+        check(y, oracle.resize_aa(h, s[0], s[1], code), dtype, code, float(np.abs(h).max()),
+              f"batched antialias {m} {h.shape}->{s}")
+        if dtype != "f32":
+            assert torch.equal(rs.resize(x, s, m, antialias=True), y), (m, h.shape, s)
+    plan_outs = [torch.zeros_like(y) for y in outs]
+    plan = rs.BatchedPlan(srcs, plan_outs, methods, antialias=True)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(plan_outs, outs))
+    tiled = rs.resize_batched(srcs, sizes, methods, antialias=True, impl="tiled")
+    torch.cuda.synchronize()
+    for s, m, y, h in zip(sizes, methods, tiled, host):
+        code = rs.METHODS[m]
+        check(y, oracle.resize_aa(h, s[0], s[1], code), dtype, code, float(np.abs(h).max()),
+              f"batched antialias tiled {m} {h.shape}->{s}")
+    with pytest.raises(rs.ResampleError):   # nearest has no antialias filter
+        rs.resize_batched(srcs[:2], sizes[:2], ["nearest", "bilinear"], antialias=True)
+    assert rs.debug_fault() == 0
