@@ -590,10 +590,40 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     __syncthreads();   // chunk 0 and the position table visible
     issue(2);
 
+    // One channel: a thread's KX taps are consecutive floats, read as KX / 2
+    // + 1 8-byte pairs from the even float at or below the first tap (the
+    // odd-offset threads take the taps one float on), so neighbouring
+    // threads' taps, two floats apart at a x2 upscale, cost no bank conflicts.
+    // The last pair may reach one float past the staged row (still inside
+    // the block's shared memory) and is then not used.
+    constexpr bool pairs = C == 1 && KX % 2 == 0;
+    int pb[2];
+    bool podd[2];
+    #pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        pb[k] = off[k] & ~1;
+        podd[k] = off[k] & 1;
+    }
     auto hrow = [&](const float* Sr, float2& h) {
         h = make_float2(0.0f, 0.0f);
-        #pragma unroll
-        for (int q = 0; q < KX; ++q) h = __ffma2_rn(wxp[q], make_float2(Sr[off[0] + q * C], Sr[off[1] + q * C]), h);
+        if constexpr (pairs) {
+            float e[2][KX + 2];
+            #pragma unroll
+            for (int k = 0; k < 2; ++k)
+                #pragma unroll
+                for (int t = 0; t < KX / 2 + 1; ++t) {
+                    const float2 v = reinterpret_cast<const float2*>(Sr + pb[k])[t];
+                    e[k][2 * t] = v.x;
+                    e[k][2 * t + 1] = v.y;
+                }
+            #pragma unroll
+            for (int q = 0; q < KX; ++q)
+                h = __ffma2_rn(wxp[q], make_float2(podd[0] ? e[0][q + 1] : e[0][q], podd[1] ? e[1][q + 1] : e[1][q]), h);
+        } else {
+            #pragma unroll
+            for (int q = 0; q < KX; ++q)
+                h = __ffma2_rn(wxp[q], make_float2(Sr[off[0] + q * C], Sr[off[1] + q * C]), h);
+        }
     };
     float2 h[KY];
     #pragma unroll

@@ -508,22 +508,29 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
     constexpr bool can_vec = !NORM && (PB == 4 || PB == 8 || PB == 16 || (PB == 2 && ES == 1));
     const bool vec0 = can_vec && (reinterpret_cast<uintptr_t>(dband) % PB) == 0;
     const bool vec_all = ((g.dst_pitch * EO) % PB) == 0;   // every row keeps row 0's alignment
+    // (every pixel of the lane valid: one straight-line run of stores)
+    const bool all_valid = valid[P - 1];
+    auto put_px = [&](TO* p, int m, const float2 (&v)[NP][C], bool vec) {
+        float x[C];
+        #pragma unroll
+        for (int c = 0; c < C; ++c) x[c] = (m & 1) ? v[m >> 1][c].y : v[m >> 1][c].x;
+        if constexpr (NORM) {
+            #pragma unroll
+            for (int c = 0; c < C; ++c) Store<TO>::put(p + c * no.c_stride + 32 * m, fmaf(x[c], no.scale[c], no.bias[c]));
+        } else {
+            win_store_px<C, T>(p + 32 * m * C, x, vec);
+        }
+    };
     auto put = [&](int row, const float2 (&v)[NP][C]) {
         TO* p = dband + row * pitch32;
         const bool vec = can_vec && (vec_all ? vec0 : (reinterpret_cast<uintptr_t>(p) % PB) == 0);
-        #pragma unroll
-        for (int m = 0; m < P; ++m) {
-            if (valid[m]) {
-                float x[C];
-                #pragma unroll
-                for (int c = 0; c < C; ++c) x[c] = (m & 1) ? v[m >> 1][c].y : v[m >> 1][c].x;
-                if constexpr (NORM) {
-                    #pragma unroll
-                    for (int c = 0; c < C; ++c) Store<TO>::put(p + c * no.c_stride + 32 * m, fmaf(x[c], no.scale[c], no.bias[c]));
-                } else {
-                    win_store_px<C, T>(p + 32 * m * C, x, vec);
-                }
-            }
+        if (all_valid) {
+            #pragma unroll
+            for (int m = 0; m < P; ++m) put_px(p, m, v, vec);
+        } else {
+            #pragma unroll
+            for (int m = 0; m < P; ++m)
+                if (valid[m]) put_px(p, m, v, vec);
         }
     };
 
