@@ -62,11 +62,15 @@ def parse():
                          "2..10, the paper's kernel (one thread per output pixel) over block shapes, against "
                          "AUTO; prints a markdown table and exits")
     ap.add_argument("--ops-only", nargs="?", const="batch", default=None,
-                    choices=["batch", "rgb", "nchw", "backward", "float"],
+                    choices=["batch", "rgb", "nchw", "backward", "float", "sweep"],
                     help="profiling driver: run warmup + steps untimed launches of the 256-image batch plan "
                          "(batch, the default), of the three RGB 4096 resizes (rgb), of the NCHW FP32 forward "
-                         "or backward x2 / x0.5 (nchw, backward) or of the float 8192 bicubic x2 in FP32 / "
-                         "FP16 / BF16 (float), and exit")
+                         "or backward x2 / x0.5 (nchw, backward), of the float 8192 bicubic x2 in FP32 / "
+                         "FP16 / BF16 (float) or of the paper's kernel with 32x4 and 4x32 blocks on the "
+                         "800x800 uint8 bilinear x4 of the tiling study (sweep), and exit")
+    ap.add_argument("--flush-between", action="store_true",
+                    help="profiling drivers only: write a 256 MB buffer after every launch, so that the next "
+                         "launch's DRAM writes show the L2 write-back of the previous launch's output")
     ap.add_argument("--batch-images", type=int, default=256,
                     help="profiling drivers only: the first N images of the batch (a smaller capture)")
     return ap.parse_args()
@@ -175,7 +179,7 @@ class ClockSampler:
 # Source files each profiled kernel is built from (a change to any of them
 # voids its recorded DRAM traffic).
 KERNEL_SOURCES = {
-    "k_batched_window": ["batched.cu", "win_body.cuh", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
+    "k_batched_window": ["batched.cu", "win_body.cuh", "tile_body.cuh", "aa_wide.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_win": ["win.cu", "win_body.cuh", "rs_common.cuh", "rs_internal.h"],
     "k_stream": ["stream.cu", "rs_common.cuh", "rs_internal.h"],
     "k_tiled": ["tiled.cu", "tile_body.cuh", "rs_common.cuh", "rs_internal.h"],
@@ -312,6 +316,10 @@ def profile_ops(args, torch, rs, workloads, dev):
             Ho = out_hw(4096, s)
             y = torch.empty((Ho, Ho, 3), dtype=torch.uint8, device=dev)
             ops.append(lambda y=y, m=method, Ho=Ho: rs.resize(x, (Ho, Ho), m, out=y))
+    elif args.ops_only == "sweep":
+        x = torch.from_numpy(workloads.uniform_u8(6, 800, 800, 1)).to(dev)
+        y = torch.empty((3200, 3200, 1), dtype=torch.uint8, device=dev)
+        ops = [lambda t=t: rs.resize(x, (3200, 3200), "bilinear", out=y, impl="plain", tile=t) for t in ((32, 4), (4, 32))]
     elif args.ops_only == "float":
         f64 = workloads.workload_float_8192(seed=3)
         ops = []
@@ -321,12 +329,21 @@ def profile_ops(args, torch, rs, workloads, dev):
             ops.append(lambda xf=xf, yf=yf: rs.resize(xf, (16384, 16384), "bicubic", out=yf))
     else:
         b = Batch(torch, workloads, dev, args.batch_images)
+        if not args.no_autotune:   # the item shape the timed plan uses
+            rs.autotune_batched(b.srcs, b.outs, b.methods)
         plan = rs.BatchedPlan(b.srcs, b.outs, b.methods)
         ops = [plan.launch]
+    flush = Flusher(torch, dev) if args.flush_between else None
+    torch.cuda.synchronize()
+    # the launches below, alone, under `ncu --profile-from-start off`
+    torch.cuda.profiler.start()
     for _ in range(args.warmup + args.steps):
         for fn in ops:
             fn()
+            if flush:
+                flush()
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
 
 
 def run_ours(args, rank, world, local):
