@@ -342,6 +342,21 @@ static rs_status prepare_image(const rs_image_desc& x, int dtype, const rs_optio
     return RS_OK;
 }
 
+// Items of one image (as prepare_image counts them) and a rough cost of one
+// item: its output rows and the source rows they stage (per strip or tile
+// column), plus a fixed part for the block's prologue.
+static int64_t image_items(const BatchImage& im)
+{
+    const int rows = im.kind == 1 ? im.band_h : im.kind == 2 ? im.TH : im.tile_h;
+    return (int64_t)im.tiles_x * ((im.Ho + rows - 1) / rows);
+}
+
+static double item_cost(const BatchImage& im)
+{
+    const int rows = im.kind == 1 ? im.band_h : im.kind == 2 ? im.TH : im.tile_h;
+    return rows * (1.0 + 0.55 * (double)im.H / (double)im.Ho) + 24.0;
+}
+
 // Work-list layout shared by the workspace and the fixed-array paths:
 // descriptors grouped by class (class c occupies [first[c], first[c] +
 // count[c])), then per class an exclusive prefix of count[c] + 1 entries
@@ -453,12 +468,22 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
         fill[c] = 0;
         start_out[L.prefix[c]] = 0;
     }
-    for (int k = 0; k < n; ++k) {   // stable: images keep their order within a class
+    for (int k = 0; k < n; ++k) {
         const int c = tmp_cls[k];
-        const int pos = fill[c]++;
-        imgs_out[L.first[c] + pos] = tmp_imgs[k];
+        imgs_out[L.first[c] + fill[c]++] = tmp_imgs[k];
+    }
+    // Within a class, images with the costliest items first: block b takes
+    // items b, b + grid, ..., so neighbouring items of similar cost spread
+    // evenly over the blocks and the launch ends with the cheap ones.
+    for (int c = 0; c < kClasses; ++c) {
+        BatchImage* first = imgs_out + L.first[c];
+        std::sort(first, first + L.count[c], [](const BatchImage& a, const BatchImage& b) {
+            const double ka = item_cost(a), kb = item_cost(b);
+            if (ka != kb) return ka > kb;
+            return a.H * (int64_t)a.W < b.H * (int64_t)b.W;
+        });
         int64_t* st = start_out + L.prefix[c];
-        st[pos + 1] = st[pos] + tmp_items[k];
+        for (int pos = 0; pos < L.count[c]; ++pos) st[pos + 1] = st[pos] + image_items(first[pos]);
     }
     for (int c = 0; c < kClasses; ++c) L.total[c] = start_out[L.prefix[c] + L.count[c]];
     return RS_OK;
