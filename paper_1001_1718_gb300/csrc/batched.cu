@@ -365,6 +365,7 @@ struct BatchLayout {
     int count[kClasses], first[kClasses], prefix[kClasses];
     int64_t total[kClasses];
     size_t smem[kClasses];
+    double item_cost[kClasses];   // mean cost of the class's items (item_cost)
     int threads;
     int n;
 };
@@ -483,7 +484,13 @@ static rs_status batch_layout(const rs_image_desc* d, int n, int dtype, const rs
             return a.H * (int64_t)a.W < b.H * (int64_t)b.W;
         });
         int64_t* st = start_out + L.prefix[c];
-        for (int pos = 0; pos < L.count[c]; ++pos) st[pos + 1] = st[pos] + image_items(first[pos]);
+        double cost = 0.0;
+        for (int pos = 0; pos < L.count[c]; ++pos) {
+            const int64_t it = image_items(first[pos]);
+            st[pos + 1] = st[pos] + it;
+            cost += item_cost(first[pos]) * (double)it;
+        }
+        L.item_cost[c] = st[L.count[c]] > 0 ? cost / (double)st[L.count[c]] : 0.0;
     }
     for (int c = 0; c < kClasses; ++c) L.total[c] = start_out[L.prefix[c] + L.count[c]];
     return RS_OK;
@@ -555,8 +562,21 @@ struct ClassLaunch {
 static cudaError_t class_launches(const BatchLayout& L, int dtype, const rs_options& o, const void* imgs_dev,
                                   const void* start_dev, ClassLaunch* out, int& nl)
 {
+    // Classes with the costliest items first: each next class fills the SMs
+    // as the previous one's blocks finish, and the step ends on the finest
+    // items.
+    int order[kClasses];
+    for (int c = 0; c < kClasses; ++c) {   // insertion sort, stable
+        int k = c;
+        while (k > 0 && L.item_cost[order[k - 1]] < L.item_cost[c]) {
+            order[k] = order[k - 1];
+            --k;
+        }
+        order[k] = c;
+    }
     nl = 0;
-    for (int c = 0; c < kClasses; ++c) {
+    for (int oi = 0; oi < kClasses; ++oi) {
+        const int c = order[oi];
         if (L.count[c] == 0 || L.total[c] == 0) continue;
         ClassLaunch& cl = out[nl++];
         const bool aa = (o.flags & RS_FLAG_ANTIALIAS) != 0;
