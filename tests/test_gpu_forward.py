@@ -493,7 +493,8 @@ def test_antialias_window_every_dtype(rs, oracle, method, dtype):
     ragged strips, against the FP64 definition under the storage rule."""
     impl = "window" if dtype == "f32" else "auto"
     cases = [((180, 240, 3), (90, 120)), ((97, 133, 3), (49, 67)), ((300, 520, 1), (170, 300)),
-             ((40, 36, 4), (90, 72)), ((256, 200, 3), (64, 52)), ((77, 91, 2), (77, 91))]
+             ((40, 36, 4), (90, 72)), ((256, 200, 3), (64, 52)), ((77, 91, 2), (77, 91)),
+             ((3, 200, 3), (1, 100)), ((200, 3, 1), (100, 1))]
     for k, (shape, (Ho, Wo)) in enumerate(cases):
         H, W = shape[0], shape[1]
         taps = max(_aa_taps(n, m, method) for n, m in ((H, Ho), (W, Wo)))

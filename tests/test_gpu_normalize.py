@@ -100,7 +100,8 @@ def test_resize_normalize_antialias(rs, oracle, method):
     against the FP64 antialias definition followed by the normalisation."""
     cases = [((2, 240, 320, 3), (120, 160), torch.float16), ((1, 300, 410, 3), (96, 131), torch.bfloat16),
              ((3, 100, 90, 1), (100, 90), torch.float32), ((1, 720, 1280, 3), (90, 160), torch.float16),
-             ((2, 333, 250, 4), (41, 29), torch.float32)]
+             ((2, 333, 250, 4), (41, 29), torch.float32), ((1, 500, 40, 1), (20, 2), torch.bfloat16),
+             ((3, 4, 300, 3), (1, 150), torch.float16)]
     names = {torch.float16: "f16", torch.bfloat16: "bf16", torch.float32: "f32"}
     for k, (shape, (Ho, Wo), dt) in enumerate(cases):
         img = _img(500 + k, shape)
