@@ -876,12 +876,18 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
                            cudaStream_t st)
 {
     if (method != M_BILINEAR && method != M_BICUBIC) return RS_ERR_INVALID_ARG;
-    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW && o.impl != RS_IMPL_REDUCE && o.impl != RS_IMPL_TILED)
+    if (o.impl != RS_IMPL_AUTO && o.impl != RS_IMPL_WINDOW && o.impl != RS_IMPL_REDUCE && o.impl != RS_IMPL_TILED &&
+        o.impl != RS_IMPL_STREAM)
         return RS_ERR_INVALID_ARG;
     if (o.impl == RS_IMPL_TILED) {   // the many-tap tiled kernel on request
         AaWideCfg wc;
         if (!aa_wide_config(gf, method, wc)) return RS_ERR_UNSUPPORTED;
         return cuda_status(launch_aa_wide(gf, dtype, src, dst, wc, st));
+    }
+    if (o.impl == RS_IMPL_STREAM) {   // the vertical-first streaming kernel on request
+        AaVsCfg vc;
+        if (!aa_vs_config(gf, method, dtype, vc)) return RS_ERR_UNSUPPORTED;
+        return cuda_status(launch_aa_vs(gf, dtype, src, dst, vc, st));
     }
     if (dtype == DT_F32 && o.impl != RS_IMPL_WINDOW) {
         // FP32: the fused pass in its transposed roles reads the rows in place
@@ -910,6 +916,8 @@ rs_status resize_antialias(const Geom& gf, int method, int dtype, const void* sr
         return cuda_status(launch_win_aa(gf, method, dtype, src, dst, K, c, st));
     }
     if (o.impl == RS_IMPL_WINDOW) return RS_ERR_UNSUPPORTED;
+    AaVsCfg vc;
+    if (aa_vs_config(gf, method, dtype, vc)) return cuda_status(launch_aa_vs(gf, dtype, src, dst, vc, st));
     AaWideCfg wc;
     if (!aa_wide_config(gf, method, wc)) return RS_ERR_UNSUPPORTED;
     return cuda_status(launch_aa_wide(gf, dtype, src, dst, wc, st));
@@ -925,6 +933,8 @@ rs_status resize_normalize_antialias(const Geom& g, int method, int out_dtype, c
         return cuda_status(launch_win_aa_norm(g, method, out_dtype, src, dst, K, c, no, st));
     }
     if (o.impl == RS_IMPL_WINDOW) return RS_ERR_UNSUPPORTED;
+    AaVsCfg vc;
+    if (aa_vs_config(g, method, DT_U8, vc)) return cuda_status(launch_aa_vs_norm(g, out_dtype, src, dst, vc, no, st));
     AaWideCfg wc;
     if (!aa_wide_config(g, method, wc)) return RS_ERR_UNSUPPORTED;
     return cuda_status(launch_aa_wide_norm(g, out_dtype, src, dst, wc, no, st));

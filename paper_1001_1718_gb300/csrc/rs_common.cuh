@@ -257,4 +257,31 @@ __device__ __forceinline__ float aa_weight(int j, int i, int n, int m, int metho
     return wi * (tot != 0.0f ? 1.0f / tot : 1.0f);
 }
 
+// Renormalised antialias taps of output j (any count up to K): w[0, cnt)
+// and the first tap lo; cnt is returned.
+__device__ __forceinline__ int aa_taps_n(int j, int n, int m, int method, float a, int K, int& lo, float* w,
+                                         unsigned int* fault)
+{
+    int hi;
+    aa_range(j, n, m, method, lo, hi);
+    int cnt = max(0, hi - lo);
+    if (cnt > K) {   // excluded by the host
+        report_fault(fault, FAULT_BWD_TAPS);
+        cnt = K;
+    }
+    const float inv2F = 1.0f / (2.0f * (float)max(n, m));
+    const int64_t cj = (int64_t)(2 * j + 1) * n;
+    float tot = 0.0f;
+    for (int k = 0; k < cnt; ++k) {
+        const float v = aa_kernel(lo + k, m, cj, inv2F, method, a);
+        w[k] = v;
+        tot += v;
+    }
+    const float inv = tot != 0.0f ? 1.0f / tot : 1.0f;
+    for (int k = 0; k < cnt; ++k) w[k] *= inv;
+    return cnt;
+}
+
+// The work of one block: output tile (bx, by) of one plane (s, d: the
+// plane's first source / output element). Shared memory: cfg.smem bytes.
 }  // namespace rs

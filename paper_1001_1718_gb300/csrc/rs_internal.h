@@ -122,6 +122,17 @@ struct AaWideCfg {
     size_t smem;
 };
 
+// Antialiased vertical downscales, vertical pass first (aa_vs.cuh): tiles
+// of TW output columns x TH rows; KX = the most x taps of an output; NA =
+// register slots of the streamed rows (4, 6 or 8); ve = floats of a finished
+// row buffer (the widest tile footprint times the channels, rounded up to 4;
+// at most 4 per thread); nr = the most source rows of a band of TH output
+// rows; chunk = rows per copy-ring slot; raw_row = bytes per raw ring row.
+struct AaVsCfg {
+    int KX, TW, TH, NA, ve, nr, chunk, raw_row, method;
+    size_t smem;
+};
+
 // Output of the fused pre-process (rs_resize_normalize): planar channels,
 // channel c of an image at c * c_stride elements from its first element;
 // each value is the resampled FP32 value times scale[c] plus bias[c]
@@ -181,6 +192,12 @@ cudaError_t launch_win_aa_norm(const Geom& g, int method, int out_dtype, const v
 // Antialias taps beyond the window forms (aa_wide.cu): false where a
 // tile's footprint cannot fit in shared memory.
 bool aa_wide_config(const Geom& g, int method, AaWideCfg& c);
+// The vertical-first form (aa_vs.cuh): false where it does not apply (a
+// vertical upscale, too wide a footprint, too many overlapping output rows).
+bool aa_vs_config(const Geom& g, int method, int dtype, AaVsCfg& c);
+cudaError_t launch_aa_vs(const Geom& g, int dtype, const void* src, void* dst, const AaVsCfg& c, cudaStream_t st);
+cudaError_t launch_aa_vs_norm(const Geom& g, int out_dtype, const void* src, void* dst, const AaVsCfg& c,
+                              const NormOut& no, cudaStream_t st);
 cudaError_t launch_aa_wide(const Geom& g, int dtype, const void* src, void* dst, const AaWideCfg& c, cudaStream_t st);
 cudaError_t launch_aa_wide_norm(const Geom& g, int out_dtype, const void* src, void* dst, const AaWideCfg& c,
                                 const NormOut& no, cudaStream_t st);
