@@ -550,4 +550,20 @@ def test_antialias_many_taps(rs, oracle, method, dtype):
     torch.cuda.synchronize()
     check(y, oracle.resize_aa(x64, 60, 70, method), dtype, method, float(np.abs(x64).max()),
           f"antialias tiled {dtype} {MNAME[method]}")
+    # the vertical-first streaming kernel on request, few and many taps,
+    # tiles of several widths, a ragged last band, planar planes
+    for k, (shape, (Ho, Wo)) in enumerate([((90, 120, 3), (45, 150)), ((333, 1900, 3), (70, 400)),
+                                            ((200, 64, 4), (200, 30)), ((1000, 41, 1), (37, 41))]):
+        t, x64 = _src(1950 + k, shape, dtype)
+        y = rs.resize(t.cuda(), (Ho, Wo), MNAME[method], antialias=True, impl="stream")
+        torch.cuda.synchronize()
+        check(y, oracle.resize_aa(x64, Ho, Wo, method), dtype, method, float(np.abs(x64).max()),
+              f"antialias stream {dtype} {MNAME[method]} {shape}->{Ho}x{Wo}")
+    t, x64 = _src(1960, (2, 3, 300, 150), dtype)
+    y = rs.resize(t.cuda(), (61, 70), MNAME[method], layout="nchw", antialias=True, impl="stream")
+    torch.cuda.synchronize()
+    check(y, oracle.resize_aa_nchw(x64, 61, 70, method), dtype, method, float(np.abs(x64).max()),
+          f"antialias stream nchw {dtype} {MNAME[method]}")
+    with pytest.raises(rs.ResampleError):   # a vertical upscale: not the streaming form
+        rs.resize(t[0, 0].cuda(), (400, 20), MNAME[method], antialias=True, impl="stream")
     assert rs.debug_fault() == 0
