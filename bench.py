@@ -62,12 +62,14 @@ def parse():
                          "2..10, the paper's kernel (one thread per output pixel) over block shapes, against "
                          "AUTO; prints a markdown table and exits")
     ap.add_argument("--ops-only", nargs="?", const="batch", default=None,
-                    choices=["batch", "rgb", "nchw", "backward", "float", "sweep"],
+                    choices=["batch", "rgb", "nchw", "backward", "float", "sweep", "serving"],
                     help="profiling driver: run warmup + steps untimed launches of the 256-image batch plan "
                          "(batch, the default), of the three RGB 4096 resizes (rgb), of the NCHW FP32 forward "
                          "or backward x2 / x0.5 (nchw, backward), of the float 8192 bicubic x2 in FP32 / "
-                         "FP16 / BF16 (float) or of the paper's kernel with 32x4 and 4x32 blocks on the "
-                         "800x800 uint8 bilinear x4 of the tiling study (sweep), and exit")
+                         "FP16 / BF16 (float), of the paper's kernel with 32x4 and 4x32 blocks on the "
+                         "800x800 uint8 bilinear x4 of the tiling study (sweep) or of the antialiased serving "
+                         "downscales of 16 1920x1080 uint8 frames (serving: bicubic to 398x224 uint8, bilinear "
+                         "to 455x256 normalised FP16), and exit")
     ap.add_argument("--flush-between", action="store_true",
                     help="profiling drivers only: write a 256 MB buffer after every launch, so that the next "
                          "launch's DRAM writes show the L2 write-back of the previous launch's output")
@@ -320,6 +322,14 @@ def profile_ops(args, torch, rs, workloads, dev):
         x = torch.from_numpy(workloads.uniform_u8(6, 800, 800, 1)).to(dev)
         y = torch.empty((3200, 3200, 1), dtype=torch.uint8, device=dev)
         ops = [lambda t=t: rs.resize(x, (3200, 3200), "bilinear", out=y, impl="plain", tile=t) for t in ((32, 4), (4, 32))]
+    elif args.ops_only == "serving":
+        frames = torch.from_numpy(np.stack([workloads.smooth_field_u8(600 + k, 1080, 1920, 3) for k in range(16)])).to(dev)
+        y8 = torch.empty((16, 224, 398, 3), dtype=torch.uint8, device=dev)
+        yh = torch.empty((16, 3, 256, 455), dtype=torch.float16, device=dev)
+        mean_t, std_t = (123.675, 116.28, 103.53), (58.395, 57.12, 57.375)
+        ops = [lambda: rs.resize(frames, (224, 398), "bicubic", out=y8, antialias=True),
+               lambda: rs.resize_normalize(frames, (256, 455), "bilinear", mean_t, std_t, dtype=torch.float16, out=yh,
+                                           antialias=True)]
     elif args.ops_only == "float":
         f64 = workloads.workload_float_8192(seed=3)
         ops = []
@@ -666,30 +676,37 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak, b):
     # HWC uint8 -> planar FP16) against the unfused path: the library's
     # uint8 resize, then torch's permute / normalise / cast
     mean_t, std_t = (123.675, 116.28, 103.53), (58.395, 57.12, 57.375)
-    for name, (N, H, W), (Ho, Wo), method in (("frames32_1024_to_512_bilinear", (32, 1024, 1024), (512, 512), "bilinear"),
-                                              ("frames32_512_to_1024_bicubic", (32, 512, 512), (1024, 1024), "bicubic"),
-                                              ("frames16_1080p_to_256x455_bilinear", (16, 1080, 1920), (256, 455),
-                                               "bilinear")):
+    for name, (N, H, W), (Ho, Wo), method, aa in (
+            ("frames32_1024_to_512_bilinear", (32, 1024, 1024), (512, 512), "bilinear", False),
+            ("frames32_512_to_1024_bicubic", (32, 512, 512), (1024, 1024), "bicubic", False),
+            ("frames16_1080p_to_256x455_bilinear", (16, 1080, 1920), (256, 455), "bilinear", False),
+            ("frames16_1080p_to_256x455_bilinear_antialias", (16, 1080, 1920), (256, 455), "bilinear", True),
+            ("frames16_1080p_to_224x398_bicubic_antialias", (16, 1080, 1920), (224, 398), "bicubic", True)):
         frames = np.stack([workloads.smooth_field_u8(600 + k, H, W, 3) for k in range(N)])
         xf = torch.from_numpy(frames).to(dev)
         yo = torch.empty((N, 3, Ho, Wo), dtype=torch.float16, device=dev)
         try:
-            rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo)
+            rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo, antialias=aa)
         except rs.ResampleError as e:
             ex[f"normalize_{name}"] = {"unsupported": str(e)}
             continue
-        ms_f = bench(lambda: rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo), 20)
+        ms_f = bench(lambda: rs.resize_normalize(xf, (Ho, Wo), method, mean_t, std_t, dtype=torch.float16, out=yo,
+                                                 antialias=aa), 20)
         yu8 = torch.empty((N, Ho, Wo, 3), dtype=torch.uint8, device=dev)
         mt = torch.tensor(mean_t, device=dev).view(1, 3, 1, 1)
         st = torch.tensor(std_t, device=dev).view(1, 3, 1, 1)
 
         def unfused():
-            rs.resize(xf, (Ho, Wo), method, out=yu8)
+            rs.resize(xf, (Ho, Wo), method, out=yu8, antialias=aa)
             torch.sub(yu8.permute(0, 3, 1, 2).float(), mt).div_(st).to(torch.float16)
         ms_u = bench(unfused, 20)
         k0 = 0
         ys, xs = workloads.sample_points(5, Ho, Wo, 2048)
-        ref = oracle.resize_normalize(frames[k0].astype(np.float64), Ho, Wo, rs.METHODS[method], mean_t, std_t)
+        if aa:
+            ref = ((oracle.resize_aa(frames[k0].astype(np.float64), Ho, Wo, rs.METHODS[method]) -
+                    np.array(mean_t)) / np.array(std_t)).transpose(2, 0, 1)
+        else:
+            ref = oracle.resize_normalize(frames[k0].astype(np.float64), Ho, Wo, rs.METHODS[method], mean_t, std_t)
         got = yo[k0][:, torch_index(ys), torch_index(xs)].double().cpu().numpy()
         refp = ref[:, ys, xs]
         unf = ((yu8[k0].permute(2, 0, 1).double() - mt[0].double()) / st[0].double())[:, torch_index(ys), torch_index(xs)]
@@ -697,7 +714,8 @@ def extras(torch, rs, dev, stream, oracle, hbm_peak, b):
             unfused_ms=ms_u, speedup_vs_unfused=ms_u / ms_f,
             max_abs_vs_f64=float(np.abs(got - refp).max()),
             unfused_max_abs_vs_f64_before_f16=float(np.abs(unf.cpu().numpy() - refp).max()),
-            note="one pass: uint8 HWC in, FP16 NCHW out; unfused: uint8 resize, then permute / normalise / cast")
+            note="one pass: uint8 HWC in, FP16 NCHW out; unfused: uint8 resize, then permute / normalise / cast" +
+                 ("; antialiased (the stretched filter; more than 8 taps per axis run the many-tap kernel)" if aa else ""))
         del xf, yo, yu8
     torch.cuda.empty_cache()
 
