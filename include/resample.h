@@ -138,10 +138,15 @@ typedef enum { RS_IMPL_AUTO = 0, RS_IMPL_TILED = 1, RS_IMPL_PLAIN = 2, RS_IMPL_S
  *   RS_F32 with 16-byte source rows and at most 8 taps per axis: REDUCE's
  *   fused pass with these taps; otherwise, up to 8 taps per axis (bilinear
  *   down to 1/4, bicubic to 1/2), WINDOW's general form with these taps
- *   (impl RS_IMPL_WINDOW selects it and refuses more taps); beyond that,
- *   or with impl RS_IMPL_TILED, a tiled kernel that holds any number of
- *   taps (tiles of 32 output columns: the tile's footprint rows are
- *   interpolated horizontally into shared memory, then blended).
+ *   (impl RS_IMPL_WINDOW selects it and refuses more taps); beyond that, on
+ *   vertical downscales (output rows <= source rows), a vertical-first
+ *   streaming kernel (each tile's source rows copied once through a
+ *   shared-memory ring, the vertical sums kept in registers, the finished
+ *   rows blended horizontally; impl RS_IMPL_STREAM selects it, and refuses
+ *   vertical upscales), else, or with impl RS_IMPL_TILED, a tiled kernel
+ *   that holds any number of taps (tiles of 32 output columns: the tile's
+ *   footprint rows are interpolated horizontally into shared memory, then
+ *   blended).
  *   RS_NEAREST: RS_ERR_INVALID_ARG. Also for rs_resize_normalize,
  *   rs_resize_backward (the adjoint of this map) and the batch. */
 #define RS_FLAG_ANTIALIAS 1
