@@ -73,3 +73,16 @@ def check(got: torch.Tensor, ref64: np.ndarray, dtype: str, method: int, src_abs
     else:
         stats["differs_from_rounded_oracle"] = int((g != q).sum())
     return stats
+
+
+def aa_taps(n, m, method):
+    """The most antialias taps an output of the axis n -> m has, by the
+    header's integer bounds: floor(((2j+1) n -+ 2 R F + m) / (2m)), F = max(n, m),
+    cut to [0, n)."""
+    R, F = (1 if method == 1 else 2), max(n, m)
+    best = 0
+    for j in range(m):
+        a = (2 * j + 1) * n + m
+        lo, hi = max((a - 2 * R * F) // (2 * m), 0), min((a + 2 * R * F) // (2 * m), n)
+        best = max(best, hi - lo)
+    return best

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from _parity import check
+from _parity import check, aa_taps
 
 pytestmark = pytest.mark.gpu
 MN = {0: "nearest", 1: "bilinear", 2: "bicubic"}
@@ -184,8 +184,10 @@ def _aa_batch(seed, n, dtype):
 def test_batched_antialias(rs, oracle, dtype):
     """RS_FLAG_ANTIALIAS on the batch (window items and many-tap tiles in one
     call), the replayable plan and the all-tiles shape, against the FP64
-    antialias definition under the storage rule; uint8 / FP16 items equal
-    the single-image antialiased call (the same kernels' arithmetic)."""
+    antialias definition under the storage rule; uint8 / FP16 items within
+    the window forms' 8 taps per axis equal the single-image antialiased call
+    (the same kernel's arithmetic; beyond 8 taps the single-image call sums
+    y first on vertical downscales, the batch's tiles x first)."""
     srcs, sizes, methods, host = _aa_batch(31, 20, dtype)
     outs = rs.resize_batched(srcs, sizes, methods, antialias=True)
     torch.cuda.synchronize()
@@ -193,7 +195,8 @@ def test_batched_antialias(rs, oracle, dtype):
         code = rs.METHODS[m]
         check(y, oracle.resize_aa(h, s[0], s[1], code), dtype, code, float(np.abs(h).max()),
               f"batched antialias {m} {h.shape}->{s}")
-        if dtype != "f32":
+        taps = max(aa_taps(h.shape[0], s[0], code), aa_taps(h.shape[1], s[1], code))
+        if dtype != "f32" and taps <= 8:
             assert torch.equal(rs.resize(x, s, m, antialias=True), y), (m, h.shape, s)
     plan_outs = [torch.zeros_like(y) for y in outs]
     plan = rs.BatchedPlan(srcs, plan_outs, methods, antialias=True)

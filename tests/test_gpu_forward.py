@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from _parity import check, to_storage, as_f64
+from _parity import check, to_storage, as_f64, aa_taps as _aa_taps
 
 pytestmark = pytest.mark.gpu
 
@@ -469,19 +469,6 @@ def test_antialias_matches_oracle(rs, oracle, method):
         check(y, oracle.resize_aa(x.astype(np.float64), Ho, Wo, method), "f32", method, float(np.abs(x).max()),
               f"antialias hwc {MNAME[method]} -> {Ho}x{Wo}")
     assert rs.debug_fault() == 0
-
-
-def _aa_taps(n, m, method):
-    """The most antialias taps an output of the axis n -> m has, by the
-    header's integer bounds: floor(((2j+1) n -+ 2 R F + m) / (2m)), F = max(n, m),
-    cut to [0, n)."""
-    R, F = (1 if method == BL else 2), max(n, m)
-    best = 0
-    for j in range(m):
-        a = (2 * j + 1) * n + m
-        lo, hi = max((a - 2 * R * F) // (2 * m), 0), min((a + 2 * R * F) // (2 * m), n)
-        best = max(best, hi - lo)
-    return best
 
 
 @pytest.mark.parametrize("method", [BL, BC])
