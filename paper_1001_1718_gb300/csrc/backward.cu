@@ -635,12 +635,28 @@ k_adj_window(const Geom g, const float* __restrict__ dY, float* __restrict__ dX,
     float* const dband = d + (int64_t)yb * g.src_pitch + e0 + tid;
     const int pitch32 = (int)g.src_pitch;
     auto blend_put = [&](int row, const int* slot) {
+        // the row's KY weights in 16-byte (KY >= 4) or 8-byte loads: RW and
+        // its rows of KY floats are 16-byte aligned
+        float w[KY];
+        if constexpr (KY % 4 == 0) {
+            #pragma unroll
+            for (int p = 0; p < KY; p += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(RW + row * KY + p);
+                w[p] = w4.x; w[p + 1] = w4.y; w[p + 2] = w4.z; w[p + 3] = w4.w;
+            }
+        } else if constexpr (KY % 2 == 0) {
+            #pragma unroll
+            for (int p = 0; p < KY; p += 2) {
+                const float2 w2 = *reinterpret_cast<const float2*>(RW + row * KY + p);
+                w[p] = w2.x; w[p + 1] = w2.y;
+            }
+        } else {
+            #pragma unroll
+            for (int p = 0; p < KY; ++p) w[p] = RW[row * KY + p];
+        }
         float2 v = make_float2(0.0f, 0.0f);
         #pragma unroll
-        for (int p = 0; p < KY; ++p) {
-            const float w = RW[row * KY + p];
-            v = __ffma2_rn(make_float2(w, w), h[slot[p]], v);
-        }
+        for (int p = 0; p < KY; ++p) v = __ffma2_rn(make_float2(w[p], w[p]), h[slot[p]], v);
         float* q = dband + row * pitch32;
         if (nact > 0) q[0] = v.x;
         if (nact > 1) q[NT] = v.y;

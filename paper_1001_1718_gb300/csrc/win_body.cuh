@@ -537,13 +537,22 @@ __device__ __forceinline__ void win_body(const Geom& g, const T* __restrict__ s,
     // window: win[x][p][c] holds source row b + x at position b (slots rotate)
     float2 win[KT][NP][C];
     auto blend = [&](const float2* wrow, const int* slot, float2 (&v)[NP][C]) {
+        // the row's (w, w) pairs two per 16-byte load (the table and its rows
+        // are 16-byte aligned)
+        float2 wr[KT];
+        #pragma unroll
+        for (int q = 0; q < KT; q += 2) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wrow + q);
+            wr[q] = make_float2(w4.x, w4.y);
+            wr[q + 1] = make_float2(w4.z, w4.w);
+        }
         #pragma unroll
         for (int p = 0; p < NP; ++p)
             #pragma unroll
             for (int c = 0; c < C; ++c) v[p][c] = make_float2(0.0f, 0.0f);
         #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            const float2 w2 = wrow[q];
+            const float2 w2 = wr[q];
             #pragma unroll
             for (int p = 0; p < NP; ++p)
                 #pragma unroll
