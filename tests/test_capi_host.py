@@ -249,3 +249,30 @@ def test_resize_normalize_validation(L):
     o.flags = B.RS_FLAG_ANTIALIAS                                 # the antialiased form takes no chunk height
     assert call(opt=o) == B.RS_ERR_INVALID_ARG
     assert call(dst=Q + 1) == B.RS_ERR_ALIGNMENT                  # FP16 output on an odd address
+
+
+def test_backward_workspace_flags(L):
+    """rs_resize_backward_workspace on the host: RS_FLAG_ANTIALIAS sizes the
+    transposed antialias tables (at a x0.25 downscale the stretched ranges
+    put every input in more outputs than the point taps do, so the tables
+    are wider), nearest has no antialiased form, and unknown flags are
+    refused."""
+    from paper_1001_1718_gb300 import _binding as B
+    dy = L.rs_layout_nchw(1, 1, 16, 16)    # forward output (grad_out)
+    dx = L.rs_layout_nchw(1, 1, 64, 64)    # forward input (grad_in)
+    n = ctypes.c_size_t(0)
+
+    def ws(method, flags):
+        o = B.options()
+        o.flags = flags
+        st = L.rs_resize_backward_workspace(ctypes.byref(dy), ctypes.byref(dx), method, ctypes.byref(o), ctypes.byref(n))
+        return st, n.value
+
+    st0, plain = ws(B.RS_BILINEAR, 0)
+    st1, aa = ws(B.RS_BILINEAR, B.RS_FLAG_ANTIALIAS)
+    assert st0 == B.RS_OK and st1 == B.RS_OK
+    # tables: H (8 + 4 K_y) + W (8 + 4 K_x), each section 256-byte aligned, plus the FP32 intermediate
+    assert aa > plain
+    assert ws(B.RS_NEAREST, B.RS_FLAG_ANTIALIAS)[0] == B.RS_ERR_INVALID_ARG
+    assert ws(B.RS_BILINEAR, 2)[0] == B.RS_ERR_INVALID_ARG
+    assert ws(B.RS_BICUBIC, B.RS_FLAG_ANTIALIAS)[0] == B.RS_OK
