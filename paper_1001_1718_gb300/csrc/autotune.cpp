@@ -134,7 +134,9 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
     // and bands to fill the GPU) of vertical upscales, and of uint8
     // downscales (measured faster than the streaming kernel there, slower
     // for FP32): 8-row chunks when they leave room for three blocks per SM,
-    // else 4-row chunks, within ~100 KB.
+    // else 4-row chunks, within ~100 KB; two blocks per resident slot, one
+    // for a single plane's vertical downscale (fewer, longer bands measured
+    // faster there).
     const int64_t out_elems = (int64_t)g.Ho * g.Wo * g.C * g.planes;
     // FP32 vertical downscales to at least 1/4 (every source row feeds an
     // output row): the window pass in its transposed roles, within ~100 KB.
@@ -147,7 +149,7 @@ static bool default_choice(const Geom& g, int method, int dtype, const void* src
     }
     if ((g.Ho >= g.H || dtype == DT_U8) && out_elems >= (int64_t)1 << 22) {
         for (int ch : {8, 4}) {
-            const Tuned t{RS_IMPL_WINDOW, 1024, ch, 128, 2};
+            const Tuned t{RS_IMPL_WINDOW, 1024, ch, 128, g.Ho < g.H && g.planes == 1 ? 1 : 2};
             if (make_choice(g, method, dtype, src, t, k) && k.window.smem <= (ch == 8 ? 56 : 100) * 1024) return true;
         }
     }

@@ -206,7 +206,10 @@ cudaError_t launch_win(const Geom& g, int method, int dtype, const void* src, vo
     const int64_t strips = ((int64_t)g.Wo + SP - 1) / SP;
     if (c.band_h <= 0) {
         const int64_t resident = (int64_t)num_sms() * std::max(1, per_sm);
-        const int waves = c.waves > 0 ? c.waves : 2;
+        // two blocks per resident slot; one for a single plane's vertical
+        // downscale, whose bands stage several source rows per output row
+        // (fewer, longer bands measured faster there)
+        const int waves = c.waves > 0 ? c.waves : g.Ho < g.H && g.planes == 1 ? 1 : 2;
         // at most `waves` blocks per resident slot: a partial extra wave would run alone
         const int64_t bands = std::max<int64_t>(1, resident * waves / (strips * g.planes));
         c.band_h = (int)std::min<int64_t>(c.band_cap, std::max<int64_t>(1, (g.Ho + bands - 1) / bands));
