@@ -1,6 +1,8 @@
 // Antialiased resampling with more taps per axis than the register-window
-// forms hold: the single-image kernels (every storage dtype, and the fused
-// pre-process's normalised planar output) and the host configuration.
+// forms hold: the single-image kernels of the vertical-first streaming form
+// (aa_vs.cuh, vertical downscales) and of the tiled form (aa_wide.cuh, any
+// ratio), for every storage dtype and for the fused pre-process's
+// normalised planar output, and their host configuration.
 #include <algorithm>
 #include <vector>
 
