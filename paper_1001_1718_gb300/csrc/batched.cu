@@ -802,7 +802,8 @@ rs_status rs_batched_plan_create(const rs_image_desc* d, int n, rs_dtype dtype, 
     for (int i = 0; i < nl && e == cudaSuccess; ++i) {
         ClassLaunch& c = cls[i];
         void* args[] = {&c.imgs, &c.start, &c.n, &c.total, &c.coord, &c.a, &c.fault};
-        cudaKernelNodeParams kp{};
+        cudaKernelNodeParams kp;
+        std::memset(&kp, 0, sizeof kp);
         kp.func = c.func;
         kp.gridDim = c.grid;
         kp.blockDim = c.block;
