@@ -228,8 +228,9 @@ rs_status rs_resize_ex(const void* src, const rs_layout* in, void* dst,
  * stddev[c]. mean, stddev: C host floats each (finite, stddev nonzero). Options: coord and
  * cubic_a as for rs_resize_ex; impl RS_IMPL_AUTO or RS_IMPL_WINDOW (the
  * register-window kernel; tile_h = staged rows per chunk, waves); flags 0
- * or RS_FLAG_ANTIALIAS (the antialiased window form up to 8 taps per axis,
- * the many-tap tiled kernel beyond unless impl is RS_IMPL_WINDOW; tile_h
+ * or RS_FLAG_ANTIALIAS (the antialiased window form up to 8 taps per axis;
+ * beyond that, unless impl is RS_IMPL_WINDOW, the vertical-first streaming
+ * kernel on vertical downscales, else the many-tap tiled kernel; tile_h
  * must be 0). RS_NEAREST returns RS_ERR_UNSUPPORTED, and so does a point-
  * sampled downscale whose staged footprint exceeds shared memory (about
  * 1/5 and below; RS_FLAG_ANTIALIAS is the filter for such downscales).
